@@ -1,0 +1,171 @@
+/*
+ * gd.h -- exact 3- and 4-node graphlet decomposition on one GB300 (sm_103a).
+ *
+ * C ABI of libgd.so.  Plain pointers and sizes only.
+ *
+ * Paper: N. K. Ahmed, J. Neville, R. A. Rossi, N. Duffield, T. L. Willke,
+ * "Graphlet Decomposition: Framework, Algorithms, and Applications" (2015),
+ * arXiv:1506.04322.
+ *
+ * Problem (Sec. 2.1, problem statement and Definitions 1-2): for an undirected
+ * simple graph G = (V, E), count the k-node subsets of V whose induced
+ * subgraph is isomorphic to each graphlet of size k = 3 and k = 4 (4 and 11
+ * graphlets, Table 1).  The method (Sec. 3-4, Algorithms 1-2) visits every
+ * edge e = (u, v) once, finds Tri_e = N(u) n N(v) and the star sets
+ * Star_u, Star_v, counts 4-cliques and 4-cycles through e directly
+ * (CliqueCount, CycleCount), adds the unrestricted counts of Sec. 4.2 and
+ * completes the rest with the Lemmas of Sec. 4.3 and the equations for g4_9
+ * and g4_11.
+ *
+ * Result order (Table 1 numbering), used by every call that returns counts:
+ *   index  0  1  2  3  4  5  6  7  8  9  10 11 12 13   14
+ *          g31 g32 g33 g34 g41 g42 g43 g44 g45 g46 g47 g48 g49 g4_10 g4_11
+ *   g31 triangle, g32 2-star, g33 3-node-1-edge, g34 3-node-independent,
+ *   g41 4-clique, g42 4-chordal-cycle, g43 4-tailed-triangle, g44 4-cycle,
+ *   g45 3-star, g46 4-path, g47 4-node-1-triangle, g48 4-node-2-star,
+ *   g49 4-node-2-edge, g4_10 4-node-1-edge, g4_11 4-node-independent.
+ *
+ * Input graph format (all calls): CSR with n rows, row_ptr int32[n+1]
+ * (row_ptr[0] = 0, non-decreasing), col_idx int32[nnz] with nnz = row_ptr[n]
+ * = 2|E|: both directions of every edge are stored, each row strictly
+ * ascending, no self-loops, every id in [0, n).  |V| = n counts isolated rows
+ * (Sec. 3.2 uses |V| in the counts of g33 / g34).
+ *
+ * Arithmetic: exact integers only.  Global counts are unsigned 128-bit
+ * (C(n,4) exceeds 2^64 for n > ~1.1e5); per-edge counts are uint64.
+ *
+ * Error behaviour: every call returns a gd_status.  On failure no output is
+ * written (a per-edge output buffer may hold partial data) and the context's
+ * last-error text (gd_last_error) says why.  GD_ECUDA means a CUDA runtime
+ * error; the context should then be destroyed.
+ *
+ * Threading: calls on one context are not thread-safe; use one context per
+ * host thread, except gd_submit / gd_poll which may be called from one
+ * producer thread while the service thread runs.
+ */
+#ifndef GD_H
+#define GD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Exact unsigned 128-bit integer: value = lo + 2^64 * hi. */
+typedef struct gd_u128 { uint64_t lo, hi; } gd_u128;
+
+typedef struct gd_ctx gd_ctx;
+typedef struct gd_graph gd_graph;
+typedef uint64_t gd_req;
+
+typedef enum gd_status {
+    GD_OK = 0,
+    GD_EINVAL = 1,      /* bad argument, or CSR not simple/sorted/symmetric */
+    GD_ENOMEM = 2,      /* host or device allocation failed, or over budget */
+    GD_ECUDA = 3,       /* CUDA runtime error (see gd_last_error)           */
+    GD_EAGAIN = 4,      /* gd_poll: request not finished yet               */
+    GD_ETIMEDOUT = 5,   /* a bounded device-side wait gave up              */
+    GD_EOVERFLOW = 6,   /* n or nnz beyond int32 ids                        */
+    GD_ENOTIMPL = 7,    /* option combination not available                 */
+    GD_EARITH = 8       /* an exact division left a remainder (internal)    */
+} gd_status;
+
+/* gd_create_csr flags */
+enum {
+    GD_DEVICE_PTRS = 1,  /* row_ptr / col_idx are device pointers            */
+    GD_VALIDATE = 2,     /* check the CSR (sorted, simple, symmetric) first  */
+    GD_BORROW = 4        /* with GD_DEVICE_PTRS: use the caller's arrays in
+                            place (caller keeps them alive and unchanged until
+                            gd_destroy_graph) instead of copying them         */
+};
+
+/* gd_count_per_edge output flags */
+enum { GD_OUT_DEVICE = 1 };
+
+/* How the 4-node direct counts of Step 2 are obtained (Sec. 4.4). */
+typedef enum gd_variant {
+    GD_VARIANT_AUTO = 0,     /* fastest exact variant for the graph           */
+    GD_VARIANT_LITERAL = 1,  /* per edge: CliqueCount scans the lists of Tri_e,
+                                CycleCount scans the lists of Star_u exactly as
+                                Algorithm 2 (cost sum over Star_u of degrees)  */
+    GD_VARIANT_ORIENTED = 2  /* every 4-clique and 4-cycle enumerated once under
+                                a degree ordering and credited to its edges;
+                                cyc_e from 4-cycle counts via the restricted-
+                                count identities (identical results)         */
+} gd_variant;
+
+typedef struct gd_options {
+    int32_t variant;          /* gd_variant (default AUTO)                         */
+    int32_t block_threads;    /* threads per CTA of the edge kernels (default 256) */
+    int32_t ctas_per_sm;      /* persistent CTAs per SM (default: occupancy)       */
+    int32_t smem_table_max;   /* wedge-table entries kept in shared memory per CTA
+                                 before the global table is used (default 12288) */
+    int32_t reserved[8];
+} gd_options;
+
+/* Fill *opt with the defaults. */
+void gd_default_options(gd_options *opt);
+
+/* Create a context on CUDA device `device`.  hbm_budget_bytes = 0: no limit;
+ * otherwise graphs whose device footprint would exceed the budget are refused
+ * with GD_ENOMEM.  opt may be NULL (defaults).  *ctx receives the handle. */
+int gd_init(gd_ctx **ctx, int device, size_t hbm_budget_bytes, const gd_options *opt);
+
+/* Destroy a context and every graph still attached to it. */
+void gd_destroy(gd_ctx *ctx);
+
+/* Text of the last error on this context ("" if none).  Valid until the next
+ * call on the context. */
+const char *gd_last_error(gd_ctx *ctx);
+
+/* Upload (or adopt, with GD_DEVICE_PTRS|GD_BORROW) a CSR graph.  n rows,
+ * nnz = row_ptr[n] entries.  cuda_stream (a cudaStream_t, may be NULL for the
+ * legacy default stream) is the stream every later call on this graph uses.
+ * GD_VALIDATE runs the full check (sorted rows, no self-loops/duplicates,
+ * symmetric) and returns GD_EINVAL with the first violation; without it only
+ * O(n) checks of row_ptr are made.  *out receives the handle. */
+int gd_create_csr(gd_ctx *ctx, int32_t n, int64_t nnz, const int32_t *row_ptr,
+                  const int32_t *col_idx, int flags, void *cuda_stream, gd_graph **out);
+
+/* n and |E| of a graph. */
+int gd_graph_info(const gd_graph *g, int32_t *n, int64_t *m);
+
+/* Bytes of device memory the graph holds now (CSR + per-graph work arrays). */
+int gd_graph_footprint(const gd_graph *g, size_t *bytes);
+
+/* Release a graph (device memory included). */
+void gd_destroy_graph(gd_graph *g);
+
+/* Global counts of all 15 graphlets of size 3 and 4 (Algorithm 2 result).
+ * out: host array of 15 gd_u128.  Synchronous. */
+int gd_count_global(gd_graph *g, gd_u128 out[15]);
+
+/* Per-edge counts: for every edge e = (u, v), u < v, in CSR order (row u
+ * ascending, then v ascending), the number of induced 3- and 4-node subsets
+ * that contain u and v and are isomorphic to each graphlet (Corollaries 1-14
+ * evaluated per edge).  out: uint64[|E|][15] row-major, host memory, or
+ * device memory if out_flags has GD_OUT_DEVICE.  Columns g34 and g4_11 are 0
+ * by definition (those graphlets have no edge).  global_out (host, nullable)
+ * receives the global counts too.  Synchronous. */
+int gd_count_per_edge(gd_graph *g, uint64_t *out, int out_flags, gd_u128 global_out[15]);
+
+/* Batch of independent graphs packed in one CSR: graph i owns node ids
+ * graph_node_ptr[i] .. graph_node_ptr[i+1]-1, and its edges stay inside that
+ * range.  row_ptr has graph_node_ptr[num_graphs]+1 entries, col_idx holds
+ * global node ids.  out: uint64[num_graphs][15] per-graph global counts
+ * (host memory, or device memory with GD_OUT_DEVICE in flags).  Every
+ * graph's counts fit uint64 when it has at most 65,535 nodes; a larger
+ * graph in the batch is refused with GD_EOVERFLOW.  flags: GD_DEVICE_PTRS
+ * (inputs on the device), GD_VALIDATE, GD_OUT_DEVICE.  Runs on the context's
+ * stream.  Synchronous. */
+int gd_count_batch(gd_ctx *ctx, int32_t num_graphs, const int32_t *graph_node_ptr,
+                   const int32_t *row_ptr, const int32_t *col_idx, int flags,
+                   uint64_t *out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GD_H */
