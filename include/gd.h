@@ -75,7 +75,8 @@ typedef enum gd_status {
 /* gd_create_csr flags */
 enum {
     GD_DEVICE_PTRS = 1,  /* row_ptr / col_idx are device pointers            */
-    GD_VALIDATE = 2,     /* check the CSR (sorted, simple, symmetric) first  */
+    GD_VALIDATE = 2,     /* accepted for clarity: the full CSR check (sorted,
+                            simple, symmetric, ids in range) always runs     */
     GD_BORROW = 4        /* with GD_DEVICE_PTRS: use the caller's arrays in
                             place (caller keeps them alive and unchanged until
                             gd_destroy_graph) instead of copying them         */
@@ -123,9 +124,10 @@ const char *gd_last_error(gd_ctx *ctx);
 /* Upload (or adopt, with GD_DEVICE_PTRS|GD_BORROW) a CSR graph.  n rows,
  * nnz = row_ptr[n] entries.  cuda_stream (a cudaStream_t, may be NULL for the
  * legacy default stream) is the stream every later call on this graph uses.
- * GD_VALIDATE runs the full check (sorted rows, no self-loops/duplicates,
- * symmetric) and returns GD_EINVAL with the first violation; without it only
- * O(n) checks of row_ptr are made.  *out receives the handle. */
+ * The CSR is always checked on the device (row bounds, strictly ascending
+ * rows, ids in range, no self-loops, every edge stored in both directions);
+ * a violation returns GD_EINVAL naming the first bad row.  The check costs
+ * one binary search per stored entry.  *out receives the handle. */
 int gd_create_csr(gd_ctx *ctx, int32_t n, int64_t nnz, const int32_t *row_ptr,
                   const int32_t *col_idx, int flags, void *cuda_stream, gd_graph **out);
 

@@ -551,7 +551,6 @@ static int o2_raw(int32_t n, const int32_t *rp, const int32_t *ci, int threads, 
         int32_t *tmark = (int32_t *)calloc((size_t)n + 1, sizeof(int32_t));
         int32_t *pos_b = (int32_t *)malloc(((size_t)n + 1) * sizeof(int32_t));
         int32_t *trl = (int32_t *)malloc(((size_t)n + 1) * sizeof(int32_t));
-        int64_t tick = 0;
         #pragma omp for schedule(dynamic, 16)
         for (int32_t a = 0; a < n; a++) {
             if (!stamp || !pos_a || !tmark || !pos_b || !trl) continue;
@@ -560,20 +559,20 @@ static int o2_raw(int32_t n, const int32_t *rp, const int32_t *ci, int threads, 
             for (int32_t p = rp[a]; p < rp[a + 1]; p++) {
                 int32_t b = ci[p];
                 if (!rank_less(rp, a, b)) continue;
-                /* Tri+ = N+(a) n N+(b) */
-                tick++;
+                /* Tri+ = N+(a) n N+(b), ascending ids */
                 int32_t nt = 0;
                 for (int32_t q = rp[b]; q < rp[b + 1]; q++) {
                     int32_t c = ci[q];
-                    if (rank_less(rp, b, c) && stamp[c] == a + 1) {
-                        tmark[c] = (int32_t)tick; pos_b[c] = q; trl[nt++] = c;
-                    }
+                    if (rank_less(rp, b, c) && stamp[c] == a + 1) { pos_b[c] = q; trl[nt++] = c; }
                 }
+                /* pairs {c, d} of Tri+ joined by an edge: binary search of
+                 * the later one in the earlier one's list */
                 for (int32_t i = 0; i < nt; i++) {
                     int32_t c = trl[i];
-                    for (int32_t q = rp[c]; q < rp[c + 1]; q++) {
-                        int32_t d = ci[q];
-                        if (tmark[d] != (int32_t)tick || !rank_less(rp, c, d)) continue;
+                    for (int32_t j = i + 1; j < nt; j++) {
+                        int32_t d = trl[j];
+                        int32_t q = find_slot(rp, ci, c, d);
+                        if (q < 0) continue;
                         /* 4-clique {a, b, c, d} */
                         atomic_add_u64(&cliq[eid[p]], 1);
                         atomic_add_u64(&cliq[eid[pos_a[c]]], 1);

@@ -1,0 +1,394 @@
+// gd_api.cu -- the C ABI of libgd (declared in include/gd.h): contexts,
+// graphs, device memory, validation and the count calls.  Every step of the
+// counting runs in the kernels of gd_count.cu / gd_batch.cu; this file only
+// allocates, orders launches and reports errors.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "gd_internal.h"
+
+using namespace gdi;
+
+namespace {
+
+int fail(gd_ctx *ctx, int code, const char *fmt, ...) {
+    if (ctx) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof(buf), fmt, ap);
+        va_end(ap);
+        ctx->err = buf;
+    }
+    return code;
+}
+
+int cuda_fail(gd_ctx *ctx, cudaError_t e, const char *where) {
+    return fail(ctx, GD_ECUDA, "%s: %s (%s)", where, cudaGetErrorString(e), cudaGetErrorName(e));
+}
+
+#define GD_CK(ctx, call)                                              \
+    do {                                                              \
+        cudaError_t e_ = (call);                                      \
+        if (e_ != cudaSuccess) return cuda_fail((ctx), e_, #call);    \
+    } while (0)
+
+// Device allocation accounted against the context budget.
+int dalloc(gd_graph *g, void **p, size_t bytes) {
+    gd_ctx *ctx = g->ctx;
+    if (bytes == 0) bytes = 16;
+    if (ctx->budget && ctx->in_use + bytes > ctx->budget)
+        return fail(ctx, GD_ENOMEM, "device budget exceeded: need %zu more bytes, %zu of %zu in use",
+                    bytes, ctx->in_use, ctx->budget);
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return fail(ctx, GD_ENOMEM, "cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
+    }
+    ctx->in_use += bytes;
+    g->ws.bytes += bytes;
+    return GD_OK;
+}
+
+template <typename T>
+int dalloc_n(gd_graph *g, T **p, int64_t count) {
+    return dalloc(g, (void **)p, sizeof(T) * (size_t)std::max<int64_t>(count, 1));
+}
+
+void free_workspace(gd_graph *g) {
+    Workspace &w = g->ws;
+    void *ptrs[] = {w.first_up, w.eoff, w.eu, w.ev, w.eslot, w.mate, w.tslot, w.tnode, w.s1, w.au, w.av,
+                    w.dt, w.cacc, w.yacc, w.vlist, w.counters, w.tribuf, w.wtab, w.sums, w.result,
+                    w.status, w.scan_tmp, w.out_buf};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    if (g->ctx) g->ctx->in_use -= std::min(g->ctx->in_use, w.bytes);
+    w = Workspace();
+}
+
+int32_t tricap_for(gd_graph *g, int variant) {
+    int64_t cap = g->max_deg;
+    if (variant != GD_VARIANT_LITERAL) {
+        // |Tri+(a,b)| <= out-degree of b <= sqrt(2|E|) under the degree order
+        int64_t s = (int64_t)std::ceil(std::sqrt((double)g->nnz)) + 1;
+        cap = std::min(cap, s);
+    }
+    return (int32_t)std::max<int64_t>(cap, 1);
+}
+
+// Allocate everything a count call needs (kept across calls; contents are
+// recomputed by every call).
+int ensure_workspace(gd_graph *g, bool per_edge, int variant) {
+    Workspace &w = g->ws;
+    const int64_t n = g->n, m = g->m, nnz = g->nnz;
+    const int sms = g->ctx->num_sms;
+    int rc;
+    if (!w.status) {
+        if ((rc = dalloc_n(g, &w.status, 4))) return rc;
+        GD_CK(g->ctx, cudaMemset(w.status, 0, 4 * sizeof(int32_t)));
+    }
+    if (!w.first_up) {
+        if ((rc = dalloc_n(g, &w.first_up, n))) return rc;
+        if ((rc = dalloc_n(g, &w.eoff, n + 1))) return rc;
+        if ((rc = dalloc_n(g, &w.eu, m))) return rc;
+        if ((rc = dalloc_n(g, &w.ev, m))) return rc;
+        if ((rc = dalloc_n(g, &w.eslot, m))) return rc;
+        if ((rc = dalloc_n(g, &w.mate, nnz))) return rc;
+        if ((rc = dalloc_n(g, &w.tslot, nnz))) return rc;
+        if ((rc = dalloc_n(g, &w.vlist, n))) return rc;
+        if ((rc = dalloc_n(g, &w.counters, 8))) return rc;
+        if ((rc = dalloc_n(g, &w.sums, 2 * (S_NUM + X_NUM)))) return rc;
+        if ((rc = dalloc_n(g, &w.result, 30))) return rc;
+        if ((rc = dalloc_n(g, &w.scan_tmp, 3 * (n + 1) + 4096))) return rc;
+        if ((rc = dalloc_n(g, &w.cacc, nnz))) return rc;
+        if ((rc = dalloc_n(g, &w.yacc, nnz))) return rc;
+    }
+    const int32_t warps = tribuf_warps(sms);
+    const int64_t need_tri = (int64_t)warps * tricap_for(g, variant) * 3;
+    if (w.tribuf_words < need_tri) {
+        if (w.tribuf) { cudaFree(w.tribuf); g->ctx->in_use -= (size_t)w.tribuf_words * 4; w.bytes -= (size_t)w.tribuf_words * 4; w.tribuf = nullptr; }
+        if ((rc = dalloc_n(g, &w.tribuf, need_tri))) return rc;
+        w.tribuf_words = need_tri;
+    }
+    if (!w.wtab && n > 0) {
+        w.wtab_ctas = sms;
+        if ((rc = dalloc_n(g, &w.wtab, (int64_t)w.wtab_ctas * n))) return rc;
+        GD_CK(g->ctx, cudaMemset(w.wtab, 0, sizeof(uint32_t) * (size_t)w.wtab_ctas * n));
+    }
+    if (per_edge && !w.tnode) {
+        if ((rc = dalloc_n(g, &w.tnode, n))) return rc;
+        if ((rc = dalloc_n(g, &w.s1, n))) return rc;
+        if ((rc = dalloc_n(g, &w.au, m))) return rc;
+        if ((rc = dalloc_n(g, &w.av, m))) return rc;
+        if ((rc = dalloc_n(g, &w.dt, m))) return rc;
+    }
+    return GD_OK;
+}
+
+int resolve_variant(gd_graph *g) {
+    int v = g->ctx->opt.variant;
+    if (v == GD_VARIANT_LITERAL) return GD_VARIANT_LITERAL;
+    return GD_VARIANT_ORIENTED;
+}
+
+int check_status(gd_graph *g, const int32_t *st) {
+    if (st[0] == 0) return GD_OK;
+    if (st[0] & ERR_CAPACITY) return fail(g->ctx, GD_EARITH, "internal: a work buffer was too small");
+    if (st[0] & ERR_TIMEOUT) return fail(g->ctx, GD_ETIMEDOUT, "a bounded device wait gave up");
+    return fail(g->ctx, GD_EARITH, "inconsistent counts (status bits 0x%x): the graph is not a simple "
+                "undirected CSR, or an internal error", st[0]);
+}
+
+int read_results(gd_graph *g, gd_u128 *out) {
+    unsigned long long res[30];
+    int32_t st[4];
+    GD_CK(g->ctx, cudaMemcpyAsync(res, g->ws.result, sizeof(res), cudaMemcpyDeviceToHost, g->stream));
+    GD_CK(g->ctx, cudaMemcpyAsync(st, g->ws.status, sizeof(st), cudaMemcpyDeviceToHost, g->stream));
+    GD_CK(g->ctx, cudaStreamSynchronize(g->stream));
+    int rc = check_status(g, st);
+    if (rc) return rc;
+    if (out)
+        for (int i = 0; i < 15; i++) { out[i].lo = res[2 * i]; out[i].hi = res[2 * i + 1]; }
+    return GD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void gd_default_options(gd_options *opt) {
+    if (!opt) return;
+    memset(opt, 0, sizeof(*opt));
+    opt->variant = GD_VARIANT_AUTO;
+    opt->block_threads = 256;
+    opt->ctas_per_sm = 0;
+    opt->smem_table_max = 8192;
+}
+
+int gd_init(gd_ctx **ctx_out, int device, size_t hbm_budget_bytes, const gd_options *opt) {
+    if (!ctx_out) return GD_EINVAL;
+    *ctx_out = nullptr;
+    gd_ctx *ctx = new (std::nothrow) gd_ctx();
+    if (!ctx) return GD_ENOMEM;
+    ctx->device = device;
+    ctx->budget = hbm_budget_bytes;
+    gd_default_options(&ctx->opt);
+    if (opt) {
+        ctx->opt = *opt;
+        int t = ctx->opt.smem_table_max;
+        if (t < 256 || t > 16384 || (t & (t - 1))) {
+            int rc = fail(ctx, GD_EINVAL, "smem_table_max must be a power of two in [256, 16384]");
+            delete ctx;
+            return rc;
+        }
+        if (ctx->opt.variant < 0 || ctx->opt.variant > 2) { delete ctx; return GD_EINVAL; }
+    }
+    cudaError_t e = cudaSetDevice(device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        delete ctx;
+        return GD_ECUDA;
+    }
+    *ctx_out = ctx;
+    return GD_OK;
+}
+
+void gd_destroy(gd_ctx *ctx) {
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    std::vector<gd_graph *> gs = ctx->graphs;
+    for (gd_graph *g : gs) gd_destroy_graph(g);
+    if (ctx->batch_buf) cudaFree(ctx->batch_buf);
+    if (ctx->stream) cudaStreamDestroy(ctx->stream);
+    delete ctx;
+}
+
+const char *gd_last_error(gd_ctx *ctx) { return ctx ? ctx->err.c_str() : "no context"; }
+
+int gd_create_csr(gd_ctx *ctx, int32_t n, int64_t nnz, const int32_t *row_ptr, const int32_t *col_idx,
+                  int flags, void *cuda_stream, gd_graph **out) {
+    if (!ctx || !out) return GD_EINVAL;
+    *out = nullptr;
+    ctx->err.clear();
+    if (n < 0 || nnz < 0) return fail(ctx, GD_EINVAL, "negative n or nnz");
+    if (n == INT32_MAX) return fail(ctx, GD_EOVERFLOW, "n must be below INT32_MAX");
+    if (nnz > INT32_MAX) return fail(ctx, GD_EOVERFLOW, "nnz %lld exceeds int32 slot ids", (long long)nnz);
+    if (nnz % 2) return fail(ctx, GD_EINVAL, "nnz is odd: an undirected CSR stores both directions");
+    if (!row_ptr || (nnz > 0 && !col_idx)) return fail(ctx, GD_EINVAL, "null CSR array");
+    const bool dev = (flags & GD_DEVICE_PTRS) != 0;
+    if ((flags & GD_BORROW) && !dev) return fail(ctx, GD_EINVAL, "GD_BORROW needs GD_DEVICE_PTRS");
+    GD_CK(ctx, cudaSetDevice(ctx->device));
+    if (!dev) {
+        // O(n) checks of row_ptr on the host
+        if (row_ptr[0] != 0) return fail(ctx, GD_EINVAL, "row_ptr[0] = %d, expected 0", row_ptr[0]);
+        for (int32_t u = 0; u < n; u++)
+            if (row_ptr[u + 1] < row_ptr[u]) return fail(ctx, GD_EINVAL, "row_ptr decreases at row %d", u);
+        if ((int64_t)row_ptr[n] != nnz) return fail(ctx, GD_EINVAL, "row_ptr[n] = %d != nnz", row_ptr[n]);
+    }
+    gd_graph *g = new (std::nothrow) gd_graph();
+    if (!g) return fail(ctx, GD_ENOMEM, "host allocation failed");
+    g->ctx = ctx;
+    g->n = n;
+    g->nnz = nnz;
+    g->m = nnz / 2;
+    g->stream = (cudaStream_t)cuda_stream;
+    ctx->graphs.push_back(g);
+    int rc = GD_OK;
+    if (dev && (flags & GD_BORROW)) {
+        g->rp = const_cast<int32_t *>(row_ptr);
+        g->ci = const_cast<int32_t *>(col_idx);
+        g->borrowed = true;
+    } else {
+        size_t bytes = sizeof(int32_t) * ((size_t)n + 1 + (size_t)nnz);
+        if (ctx->budget && ctx->in_use + bytes > ctx->budget) {
+            gd_destroy_graph(g);
+            return fail(ctx, GD_ENOMEM, "device budget exceeded by the CSR (%zu bytes)", bytes);
+        }
+        cudaError_t e = cudaMalloc((void **)&g->rp, bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            g->rp = nullptr;
+            gd_destroy_graph(g);
+            return fail(ctx, GD_ENOMEM, "cudaMalloc of the CSR failed");
+        }
+        g->csr_bytes = bytes;
+        ctx->in_use += bytes;
+        g->ci = g->rp + (n + 1);
+        cudaMemcpyKind kind = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+        e = cudaMemcpyAsync(g->rp, row_ptr, sizeof(int32_t) * ((size_t)n + 1), kind, g->stream);
+        if (e == cudaSuccess && nnz > 0)
+            e = cudaMemcpyAsync(g->ci, col_idx, sizeof(int32_t) * (size_t)nnz, kind, g->stream);
+        if (e != cudaSuccess) {
+            rc = cuda_fail(ctx, e, "CSR upload");
+            gd_destroy_graph(g);
+            return rc;
+        }
+    }
+    if ((rc = dalloc_n(g, &g->ws.status, 4))) { gd_destroy_graph(g); return rc; }
+    cudaError_t e = cudaMemsetAsync(g->ws.status, 0, 4 * sizeof(int32_t), g->stream);
+    if (e != cudaSuccess) { rc = cuda_fail(ctx, e, "status init"); gd_destroy_graph(g); return rc; }
+    if (dev) {
+        // row_ptr checks on the device copy: rp[0]==0 and rp[n]==nnz
+        int32_t ends[2] = {0, 0};
+        e = cudaMemcpyAsync(&ends[0], g->rp, sizeof(int32_t), cudaMemcpyDeviceToHost, g->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&ends[1], g->rp + n, sizeof(int32_t), cudaMemcpyDeviceToHost, g->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+        if (e != cudaSuccess) { rc = cuda_fail(ctx, e, "row_ptr read"); gd_destroy_graph(g); return rc; }
+        if (ends[0] != 0 || (int64_t)ends[1] != nnz) {
+            gd_destroy_graph(g);
+            return fail(ctx, GD_EINVAL, "row_ptr[0]=%d, row_ptr[n]=%d, nnz=%lld", ends[0], ends[1], (long long)nnz);
+        }
+    }
+    {   // the full check always runs: no kernel reads through an unchecked id
+        int32_t bad_index = -1, bad_code = 0;
+        e = validate_csr(g, &bad_index, &bad_code);
+        if (e != cudaSuccess) { rc = cuda_fail(ctx, e, "validate"); gd_destroy_graph(g); return rc; }
+        if (bad_code) {
+            gd_destroy_graph(g);
+            return fail(ctx, GD_EINVAL, "invalid CSR at row %d: rows must be strictly ascending, ids in [0,n), "
+                        "no self-loops, and every edge stored in both directions", bad_index);
+        }
+    }
+    e = max_degree(g, &g->max_deg);
+    if (e != cudaSuccess) { rc = cuda_fail(ctx, e, "max degree"); gd_destroy_graph(g); return rc; }
+    *out = g;
+    return GD_OK;
+}
+
+int gd_graph_info(const gd_graph *g, int32_t *n, int64_t *m) {
+    if (!g) return GD_EINVAL;
+    if (n) *n = g->n;
+    if (m) *m = g->m;
+    return GD_OK;
+}
+
+int gd_graph_footprint(const gd_graph *g, size_t *bytes) {
+    if (!g || !bytes) return GD_EINVAL;
+    *bytes = g->csr_bytes + g->ws.bytes;
+    return GD_OK;
+}
+
+void gd_destroy_graph(gd_graph *g) {
+    if (!g) return;
+    gd_ctx *ctx = g->ctx;
+    if (ctx) cudaSetDevice(ctx->device);
+    if (g->stream) cudaStreamSynchronize(g->stream);
+    free_workspace(g);
+    if (!g->borrowed && g->rp) {
+        cudaFree(g->rp);
+        if (ctx) ctx->in_use -= std::min(ctx->in_use, g->csr_bytes);
+    }
+    if (ctx) {
+        auto &v = ctx->graphs;
+        v.erase(std::remove(v.begin(), v.end(), g), v.end());
+    }
+    delete g;
+}
+
+int gd_count_global(gd_graph *g, gd_u128 out[15]) {
+    if (!g || !out) return GD_EINVAL;
+    gd_ctx *ctx = g->ctx;
+    ctx->err.clear();
+    GD_CK(ctx, cudaSetDevice(ctx->device));
+    const int variant = resolve_variant(g);
+    int rc = ensure_workspace(g, false, variant);
+    if (rc) return rc;
+    GD_CK(ctx, prepare_edges(g));
+    GD_CK(ctx, run_cliques_cycles(g, variant));
+    GD_CK(ctx, run_final(g, variant, false, nullptr));
+    GD_CK(ctx, run_complete(g, variant == GD_VARIANT_LITERAL ? 0 : 1));
+    return read_results(g, out);
+}
+
+int gd_count_per_edge(gd_graph *g, uint64_t *out, int out_flags, gd_u128 global_out[15]) {
+    if (!g || (!out && g->m > 0)) return GD_EINVAL;
+    gd_ctx *ctx = g->ctx;
+    ctx->err.clear();
+    GD_CK(ctx, cudaSetDevice(ctx->device));
+    const int variant = resolve_variant(g);
+    int rc = ensure_workspace(g, true, variant);
+    if (rc) return rc;
+    uint64_t *dst = out;
+    const bool dev_out = (out_flags & GD_OUT_DEVICE) != 0;
+    const size_t out_bytes = sizeof(uint64_t) * 15 * (size_t)g->m;
+    if (!dev_out) {
+        if (!g->ws.out_buf || g->ws.out_buf_bytes < out_bytes) {
+            if (g->ws.out_buf) {
+                cudaFree(g->ws.out_buf);
+                ctx->in_use -= g->ws.out_buf_bytes;
+                g->ws.bytes -= g->ws.out_buf_bytes;
+                g->ws.out_buf = nullptr;
+            }
+            if ((rc = dalloc(g, (void **)&g->ws.out_buf, out_bytes))) return rc;
+            g->ws.out_buf_bytes = out_bytes;
+        }
+        dst = g->ws.out_buf;
+    }
+    GD_CK(ctx, prepare_edges(g));
+    GD_CK(ctx, run_per_edge_sums(g));
+    GD_CK(ctx, run_cliques_cycles(g, variant));
+    GD_CK(ctx, run_final(g, variant, true, dst));
+    GD_CK(ctx, run_complete(g, 0));
+    if (!dev_out && g->m > 0)
+        GD_CK(ctx, cudaMemcpyAsync(out, dst, out_bytes, cudaMemcpyDeviceToHost, g->stream));
+    return read_results(g, global_out);
+}
+
+int gd_count_batch(gd_ctx *ctx, int32_t num_graphs, const int32_t *graph_node_ptr, const int32_t *row_ptr,
+                   const int32_t *col_idx, int flags, uint64_t *out) {
+    if (!ctx) return GD_EINVAL;
+    (void)num_graphs; (void)graph_node_ptr; (void)row_ptr; (void)col_idx; (void)flags; (void)out;
+    return fail(ctx, GD_ENOTIMPL, "gd_count_batch: not built yet");
+}
+
+}  // extern "C"

@@ -1,0 +1,875 @@
+// gd_count.cu -- single-graph kernels of the edge-centric graphlet method.
+//
+// Steps (Ahmed et al. 2015, Sec. 3-4, Algorithm 2):
+//   Step 1  per edge e=(u,v): |Tri_e| = |N(u) n N(v)|, |Star_u|, |Star_v|
+//   Step 2  per edge: cliq_e (edges inside Tri_e, Cor. 1) and cyc_e (edges
+//           between Star_u and Star_v, Cor. 3)
+//   Step 3  per edge: the unrestricted counts of Sec. 4.2 (Eqs. for
+//           N_{a,a} = C(|W|,2) and N_{a,b} = |W_a||R_b|)
+//   Step 4  sums over edges and the Lemmas of Sec. 4.3 (completion kernel)
+//
+// GPU form.  Neighbour lists are sorted int32 CSR rows.  Each undirected edge
+// is one work item (canonical slot: row u, col v > u).  Intersections are done
+// by a warp: lanes take the elements of the shorter list and binary-search the
+// longer one, so the work per edge is min(du,dv) * log(max).  Step 2 is done
+// either literally (GD_VARIANT_LITERAL: scan the lists of Tri_e / Star_u as
+// CliqueCount / CycleCount do) or by enumerating every 4-clique and 4-cycle
+// once under the degree ordering (a precedes b iff (d_a, a) < (d_b, b)) and
+// crediting the edges it contains; the per-edge cyc_e then follows from the
+// number of 4-cycles through e minus the chordal/clique cycles (identity
+// stated at run_final).  All counts are exact integers.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "gd_internal.h"
+
+namespace gdi {
+
+namespace {
+
+constexpr int WARP = 32;
+
+__device__ __forceinline__ int32_t ldg(const int32_t *p) { return __ldg(p); }
+
+__device__ __forceinline__ bool precedes(int32_t da, int32_t a, int32_t db, int32_t b) {
+    return da < db || (da == db && a < b);
+}
+
+// first index i in [0,len) with a[i] >= key (len if none)
+__device__ __forceinline__ int32_t lower_bound(const int32_t *a, int32_t len, int32_t key) {
+    int32_t lo = 0;
+    while (len > 0) {
+        int32_t half = len >> 1;
+        if (ldg(a + lo + half) < key) { lo += half + 1; len -= half + 1; }
+        else len = half;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ int32_t find_in(const int32_t *a, int32_t len, int32_t key) {
+    int32_t i = lower_bound(a, len, key);
+    return (i < len && ldg(a + i) == key) ? i : -1;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T x) {
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+}
+
+// u128 accumulation into (lo, hi) words
+__device__ __forceinline__ void add_u128(unsigned long long *lohi, unsigned long long x) {
+    if (x == 0) return;
+    unsigned long long old = atomicAdd(lohi, x);
+    if (old + x < old) atomicAdd(lohi + 1, 1ull);
+}
+
+__device__ __forceinline__ int global_warp() { return (blockIdx.x * blockDim.x + threadIdx.x) >> 5; }
+__device__ __forceinline__ int num_warps() { return (gridDim.x * blockDim.x) >> 5; }
+__device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
+
+// ---------------------------------------------------------------------------
+// CSR validation: sorted rows, ids in range, no self-loops, symmetric.
+// ---------------------------------------------------------------------------
+__global__ void k_validate(int32_t n, int64_t nnz, const int32_t *__restrict__ rp,
+                           const int32_t *__restrict__ ci, int32_t *status) {
+    for (int32_t u = blockIdx.x * blockDim.x + threadIdx.x; u < n; u += gridDim.x * blockDim.x) {
+        const int32_t b = rp[u], e = rp[u + 1];
+        // row bounds first: nothing is read through an unchecked bound
+        if (b < 0 || e < b || (int64_t)e > nnz) { atomicOr(status, ERR_CSR); atomicMin(status + 1, u); continue; }
+        for (int32_t p = b; p < e; p++) {
+            const int32_t v = ci[p];
+            bool bad = (v < 0 || v >= n || v == u || (p > b && v <= ci[p - 1]));
+            if (!bad) {
+                const int32_t vb = rp[v], ve = rp[v + 1];
+                bad = vb < 0 || ve < vb || (int64_t)ve > nnz;
+                // symmetric: u must appear in N(v)
+                if (!bad) bad = find_in(ci + vb, ve - vb, u) < 0;
+            }
+            if (bad) { atomicOr(status, ERR_CSR); atomicMin(status + 1, u); break; }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Edge list: canonical slots (u, v) with u < v, in CSR order.
+// ---------------------------------------------------------------------------
+__global__ void k_upper_count(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                              int32_t *first_up, int64_t *cnt) {
+    for (int32_t u = blockIdx.x * blockDim.x + threadIdx.x; u < n; u += gridDim.x * blockDim.x) {
+        int32_t b = rp[u], e = rp[u + 1];
+        int32_t f = b + lower_bound(ci + b, e - b, u + 1);
+        first_up[u] = f;
+        cnt[u] = e - f;
+    }
+}
+
+// exclusive scan helpers (int64), three-phase
+constexpr int SCAN_T = 256;
+constexpr int SCAN_PER = 8;
+constexpr int SCAN_TILE = SCAN_T * SCAN_PER;
+
+__global__ void k_scan_tiles(const int64_t *in, int64_t *out, int64_t len, int64_t *tile_sums) {
+    __shared__ int64_t sh[SCAN_T];
+    int64_t base = (int64_t)blockIdx.x * SCAN_TILE + threadIdx.x * SCAN_PER;
+    int64_t v[SCAN_PER];
+    int64_t s = 0;
+    for (int i = 0; i < SCAN_PER; i++) {
+        int64_t x = (base + i < len) ? in[base + i] : 0;
+        v[i] = s; s += x;
+    }
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = 1; o < SCAN_T; o <<= 1) {
+        int64_t t = (threadIdx.x >= o) ? sh[threadIdx.x - o] : 0;
+        __syncthreads();
+        sh[threadIdx.x] += t;
+        __syncthreads();
+    }
+    int64_t off = sh[threadIdx.x] - s;
+    for (int i = 0; i < SCAN_PER; i++)
+        if (base + i < len) out[base + i] = v[i] + off;
+    if (threadIdx.x == SCAN_T - 1) tile_sums[blockIdx.x] = sh[SCAN_T - 1];
+}
+
+__global__ void k_scan_add(int64_t *out, int64_t len, const int64_t *tile_offs) {
+    int64_t i = (int64_t)blockIdx.x * SCAN_TILE + threadIdx.x;
+    int64_t add = tile_offs[blockIdx.x];
+    for (int k = 0; k < SCAN_PER; k++, i += SCAN_T)
+        if (i < len) out[i] += add;
+}
+
+// exclusive scan of len values; out[len] receives the total.  tmp needs
+// >= 2 * ceil(len / SCAN_TILE) + 64 entries per level.
+cudaError_t exclusive_scan(const int64_t *in, int64_t *out, int64_t len, int64_t *tmp, cudaStream_t st) {
+    int64_t tiles = (len + SCAN_TILE - 1) / SCAN_TILE;
+    if (tiles == 0) {
+        return cudaMemsetAsync(out, 0, sizeof(int64_t), st);
+    }
+    int64_t *sums = tmp, *offs = tmp + tiles;
+    k_scan_tiles<<<(unsigned)tiles, SCAN_T, 0, st>>>(in, out, len, sums);
+    if (tiles > 1) {
+        cudaError_t e = exclusive_scan(sums, offs, tiles, tmp + 2 * tiles + 1, st);
+        if (e != cudaSuccess) return e;
+        k_scan_add<<<(unsigned)tiles, SCAN_T, 0, st>>>(out, len, offs);
+        // total = offs[tiles]
+        return cudaMemcpyAsync(out + len, offs + tiles, sizeof(int64_t), cudaMemcpyDeviceToDevice, st);
+    }
+    return cudaMemcpyAsync(out + len, sums, sizeof(int64_t), cudaMemcpyDeviceToDevice, st);
+}
+
+__global__ void k_narrow(const int64_t *in, int32_t *out, int64_t len) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < len; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = (int32_t)in[i];
+}
+
+__global__ void k_edge_list(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                            const int32_t *__restrict__ first_up, const int32_t *__restrict__ eoff,
+                            int32_t *eu, int32_t *ev, int32_t *eslot) {
+    const int lane = lane_id();
+    for (int32_t u = global_warp(); u < n; u += num_warps()) {
+        int32_t f = first_up[u], e = rp[u + 1], o = eoff[u];
+        for (int32_t i = f + lane; i < e; i += WARP) {
+            int32_t k = o + (i - f);
+            eu[k] = u; ev[k] = ci[i]; eslot[k] = i;
+        }
+    }
+}
+
+__global__ void k_mate(int64_t m, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                       const int32_t *__restrict__ eu, const int32_t *__restrict__ ev,
+                       const int32_t *__restrict__ eslot, int32_t *mate) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < m; k += (int64_t)gridDim.x * blockDim.x) {
+        int32_t u = eu[k], v = ev[k], p = eslot[k];
+        int32_t q = rp[v] + lower_bound(ci + rp[v], rp[v + 1] - rp[v], u);
+        mate[p] = q;
+        mate[q] = p;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Step 1: |Tri_e| per edge (Alg. 2 marking loops; Eq. triangle)
+// ---------------------------------------------------------------------------
+__global__ void k_triangles(int64_t m, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                            const int32_t *__restrict__ eu, const int32_t *__restrict__ ev,
+                            const int32_t *__restrict__ eslot, const int32_t *__restrict__ mate,
+                            uint32_t *tslot) {
+    const int lane = lane_id();
+    for (int64_t k = global_warp(); k < m; k += num_warps()) {
+        int32_t u = eu[k], v = ev[k];
+        int32_t bu = rp[u], du = rp[u + 1] - bu, bv = rp[v], dv = rp[v + 1] - bv;
+        int32_t sb = bu, sd = du, lb = bv, ld = dv;
+        if (dv < du) { sb = bv; sd = dv; lb = bu; ld = du; }
+        uint32_t c = 0;
+        for (int32_t i = lane; i < sd; i += WARP) {
+            int32_t x = ldg(ci + sb + i);
+            c += find_in(ci + lb, ld, x) >= 0;
+        }
+        c = warp_sum(c);
+        if (lane == 0) {
+            int32_t p = eslot[k];
+            tslot[p] = c;
+            tslot[mate[p]] = c;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Node quantities: t(x) = edges inside N(x) = sum_y T(x,y)/2; S1(x) = sum d_y
+// ---------------------------------------------------------------------------
+__global__ void k_node(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                       const uint32_t *__restrict__ tslot, uint64_t *tnode, uint64_t *s1) {
+    const int lane = lane_id();
+    for (int32_t x = global_warp(); x < n; x += num_warps()) {
+        uint64_t a = 0, b = 0;
+        for (int32_t p = rp[x] + lane; p < rp[x + 1]; p += WARP) {
+            a += tslot[p];
+            int32_t y = ci[p];
+            b += (uint64_t)(rp[y + 1] - rp[y]);
+        }
+        a = warp_sum(a); b = warp_sum(b);
+        if (lane == 0) { tnode[x] = a >> 1; s1[x] = b; }
+    }
+}
+
+// Per edge: A_u = sum_{w in Tri} T(u,w), A_v = sum_{w in Tri} T(v,w),
+// D_T = sum_{w in Tri} d_w.
+__global__ void k_tri_sums(int64_t m, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                           const int32_t *__restrict__ eu, const int32_t *__restrict__ ev,
+                           const uint32_t *__restrict__ tslot, uint64_t *au, uint64_t *av, uint64_t *dt) {
+    const int lane = lane_id();
+    for (int64_t k = global_warp(); k < m; k += num_warps()) {
+        int32_t u = eu[k], v = ev[k];
+        int32_t bu = rp[u], du = rp[u + 1] - bu, bv = rp[v], dv = rp[v + 1] - bv;
+        bool su = du <= dv;   // shorter list is u's
+        int32_t sb = su ? bu : bv, sd = su ? du : dv, lb = su ? bv : bu, ld = su ? dv : du;
+        uint64_t a_s = 0, a_l = 0, d = 0;
+        for (int32_t i = lane; i < sd; i += WARP) {
+            int32_t x = ldg(ci + sb + i);
+            int32_t j = find_in(ci + lb, ld, x);
+            if (j >= 0) {
+                a_s += tslot[sb + i];
+                a_l += tslot[lb + j];
+                d += (uint64_t)(rp[x + 1] - rp[x]);
+            }
+        }
+        a_s = warp_sum(a_s); a_l = warp_sum(a_l); d = warp_sum(d);
+        if (lane == 0) {
+            au[k] = su ? a_s : a_l;
+            av[k] = su ? a_l : a_s;
+            dt[k] = d;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Step 2, oriented: every 4-clique once, from the edge (a,b) of its two
+// lowest-ranked nodes; +1 on each of its six edges (slot credits).
+// ---------------------------------------------------------------------------
+__global__ void k_cliques_oriented(int64_t m, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                                   const int32_t *__restrict__ eu, const int32_t *__restrict__ ev,
+                                   const int32_t *__restrict__ eslot, const int32_t *__restrict__ mate,
+                                   int32_t *tribuf, int32_t tricap, unsigned long long *cacc, int32_t *status) {
+    const int lane = lane_id();
+    const int gw = global_warp();
+    int32_t *buf = tribuf + (int64_t)gw * tricap * 3;
+    for (int64_t k = gw; k < m; k += num_warps()) {
+        int32_t u = eu[k], v = ev[k];
+        int32_t du = rp[u + 1] - rp[u], dv = rp[v + 1] - rp[v];
+        int32_t p_uv = eslot[k];
+        // a precedes b
+        bool ua = precedes(du, u, dv, v);
+        int32_t a = ua ? u : v, b = ua ? v : u, db = ua ? dv : du;
+        int32_t p_ab = ua ? p_uv : mate[p_uv];
+        int32_t ba = rp[a], da = rp[a + 1] - ba, bb = rp[b];
+        // intersect N(a), N(b) (a has the smaller or equal degree)
+        int32_t cnt = 0;
+        for (int32_t i0 = 0; i0 < da; i0 += WARP) {
+            int32_t i = i0 + lane;
+            bool keep = false;
+            int32_t x = 0, j = -1;
+            if (i < da) {
+                x = ldg(ci + ba + i);
+                j = find_in(ci + bb, db, x);
+                if (j >= 0) {
+                    int32_t dx = rp[x + 1] - rp[x];
+                    keep = precedes(db, b, dx, x);
+                }
+            }
+            unsigned mask = __ballot_sync(0xffffffffu, keep);
+            int32_t pos = cnt + __popc(mask & ((1u << lane) - 1));
+            if (keep) {
+                if (pos < tricap) {
+                    buf[3 * pos] = x; buf[3 * pos + 1] = ba + i; buf[3 * pos + 2] = bb + j;
+                } else {
+                    atomicOr(status, ERR_CAPACITY);
+                }
+            }
+            cnt += __popc(mask);
+        }
+        __syncwarp();
+        if (cnt > tricap) cnt = tricap;
+        unsigned long long own = 0;
+        for (int32_t i = 0; i + 1 < cnt; i++) {
+            int32_t c = buf[3 * i], sac = buf[3 * i + 1], sbc = buf[3 * i + 2];
+            int32_t bc = rp[c], dc = rp[c + 1] - bc;
+            unsigned long long cc = 0;
+            for (int32_t j = i + 1 + lane; j < cnt; j += WARP) {
+                int32_t d = buf[3 * j];
+                int32_t q = find_in(ci + bc, dc, d);
+                if (q >= 0) {
+                    atomicAdd(cacc + (bc + q), 1ull);                 // (c,d)
+                    atomicAdd(cacc + buf[3 * j + 1], 1ull);           // (a,d)
+                    atomicAdd(cacc + buf[3 * j + 2], 1ull);           // (b,d)
+                    cc++;
+                }
+            }
+            cc = warp_sum(cc);
+            if (lane == 0 && cc) {
+                atomicAdd(cacc + sac, cc);    // (a,c)
+                atomicAdd(cacc + sbc, cc);    // (b,c)
+            }
+            own += cc;
+        }
+        if (lane == 0 && own) atomicAdd(cacc + p_ab, own);   // (a,b)
+        __syncwarp();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Step 2, oriented 4-cycles: every 4-cycle once, from its highest-ranked node
+// u with opposite node y; wedge (u, v, y) with v, y ranked below u.  A wedge
+// table counts cnt[y] = number of such v; then each wedge carries cnt[y]-1
+// cycles, credited to edges (u,v) and (v,y).  Slot credits sum, per edge, to
+// the number of (not necessarily induced) 4-cycles through the edge.
+// ---------------------------------------------------------------------------
+
+// est[u] = sum_{v in N(u), v below u} d_v  (upper bound on wedges at u)
+__global__ void k_wedge_estimate(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                                 int32_t small_cap, int32_t *vlist, int32_t *counters) {
+    const int lane = lane_id();
+    for (int32_t u = global_warp(); u < n; u += num_warps()) {
+        int32_t bu = rp[u], du = rp[u + 1] - bu;
+        int64_t est = 0;
+        int32_t dplus = 0;
+        for (int32_t i = lane; i < du; i += WARP) {
+            int32_t v = ci[bu + i];
+            int32_t dv = rp[v + 1] - rp[v];
+            if (precedes(dv, v, du, u)) est += dv; else dplus++;
+        }
+        est = warp_sum(est);
+        dplus = warp_sum(dplus);
+        if (lane == 0) {
+            atomicMax(counters + 2, dplus);
+            if (est > 0) {
+                if (est <= small_cap) {
+                    int32_t pos = atomicAdd(counters + 0, 1);
+                    vlist[pos] = u;
+                } else {
+                    int32_t pos = atomicAdd(counters + 1, 1);
+                    vlist[n - 1 - pos] = u;     // big tier fills from the back
+                }
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ uint32_t hash32(uint32_t x) {
+    x ^= x >> 16; x *= 0x7feb352dU; x ^= x >> 15; x *= 0x846ca68bU; x ^= x >> 16;
+    return x;
+}
+
+// shared-memory open-addressing table lookup (keys -1 = empty); the table
+// holds at most cap/2 keys, so every probe sequence ends.
+__device__ __forceinline__ uint32_t smem_get(const int32_t *keys, const uint32_t *vals, uint32_t capmask, int32_t y) {
+    uint32_t h = hash32((uint32_t)y) & capmask;
+    for (uint32_t probes = 0; probes <= capmask; probes++) {
+        int32_t k = keys[h];
+        if (k == y) return vals[h];
+        if (k == -1) return 0;
+        h = (h + 1) & capmask;
+    }
+    return 0;
+}
+
+template <bool GLOBAL_TABLE>
+__global__ void k_cycles_oriented(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                                  const int32_t *__restrict__ vlist_base, const int32_t *__restrict__ counters,
+                                  uint32_t capmask, uint32_t *wtab, unsigned long long *yacc) {
+    extern __shared__ int32_t sm[];
+    __shared__ int32_t ntouched;
+    int32_t *keys = sm;
+    uint32_t *vals = (uint32_t *)(sm + (capmask + 1));
+    int32_t *touched = sm + 2 * (capmask + 1);
+    // small tier: vlist_base[0 .. counters[0]); big tier: the last counters[1] entries
+    const int32_t nv = GLOBAL_TABLE ? counters[1] : counters[0];
+    const int32_t *vlist = GLOBAL_TABLE ? vlist_base + (n - nv) : vlist_base;
+    uint32_t *tab = GLOBAL_TABLE ? wtab + (int64_t)blockIdx.x * n : nullptr;
+    const int lane = lane_id(), warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    if (!GLOBAL_TABLE) {
+        for (uint32_t i = threadIdx.x; i <= capmask; i += blockDim.x) { keys[i] = -1; vals[i] = 0; }
+        if (threadIdx.x == 0) ntouched = 0;
+    }
+    __syncthreads();
+    for (int32_t idx = blockIdx.x; idx < nv; idx += gridDim.x) {
+        const int32_t u = vlist[idx];
+        const int32_t bu = rp[u], du = rp[u + 1] - bu;
+        // phase 1: count wedges per y
+        for (int32_t i = warp; i < du; i += nwarps) {
+            int32_t v = ci[bu + i];
+            int32_t bv = rp[v], dv = rp[v + 1] - bv;
+            if (!precedes(dv, v, du, u)) continue;
+            for (int32_t j = lane; j < dv; j += WARP) {
+                int32_t y = ci[bv + j];
+                int32_t dy = rp[y + 1] - rp[y];
+                if (!precedes(dy, y, du, u)) continue;
+                if (GLOBAL_TABLE) {
+                    atomicAdd(tab + y, 1u);
+                } else {
+                    uint32_t h = hash32((uint32_t)y) & capmask;
+                    while (true) {
+                        int32_t k = keys[h];
+                        if (k == y) { atomicAdd(vals + h, 1u); break; }
+                        if (k == -1) {
+                            int32_t old = atomicCAS(keys + h, -1, y);
+                            if (old == -1) {
+                                atomicAdd(vals + h, 1u);
+                                touched[atomicAdd(&ntouched, 1)] = (int32_t)h;
+                                break;
+                            }
+                            if (old == y) { atomicAdd(vals + h, 1u); break; }
+                        }
+                        h = (h + 1) & capmask;
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        // phase 2: credit cnt[y]-1 to (v,y) and (u,v)
+        for (int32_t i = warp; i < du; i += nwarps) {
+            int32_t v = ci[bu + i];
+            int32_t bv = rp[v], dv = rp[v + 1] - bv;
+            if (!precedes(dv, v, du, u)) continue;
+            unsigned long long s = 0;
+            for (int32_t j = lane; j < dv; j += WARP) {
+                int32_t y = ci[bv + j];
+                int32_t dy = rp[y + 1] - rp[y];
+                if (!precedes(dy, y, du, u)) continue;
+                uint32_t c = GLOBAL_TABLE ? tab[y] : smem_get(keys, vals, capmask, y);
+                if (c > 1) {
+                    atomicAdd(yacc + (bv + j), (unsigned long long)(c - 1));
+                    s += c - 1;
+                }
+            }
+            s = warp_sum(s);
+            if (lane == 0 && s) atomicAdd(yacc + (bu + i), s);
+        }
+        __syncthreads();
+        // phase 3: clear what this vertex touched
+        if (GLOBAL_TABLE) {
+            for (int32_t i = warp; i < du; i += nwarps) {
+                int32_t v = ci[bu + i];
+                int32_t bv = rp[v], dv = rp[v + 1] - bv;
+                if (!precedes(dv, v, du, u)) continue;
+                for (int32_t j = lane; j < dv; j += WARP) tab[ci[bv + j]] = 0;
+            }
+        } else {
+            const int32_t nt = ntouched;
+            for (int32_t i = threadIdx.x; i < nt; i += blockDim.x) {
+                int32_t h = touched[i];
+                keys[h] = -1; vals[h] = 0;
+            }
+        }
+        __syncthreads();
+        if (!GLOBAL_TABLE && threadIdx.x == 0) ntouched = 0;
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Step 2, literal (Algorithm 2 CliqueCount / CycleCount), warp per edge.
+// cliq_e: for w in Tri_e, r in N(w): r in Tri_e (each internal edge seen
+// twice; the paper's X(w)=0 reset halves it the same way).
+// cyc_e: for w in Star_u, r in N(w): r in Star_v.
+// ---------------------------------------------------------------------------
+__global__ void k_literal(int64_t m, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                          const int32_t *__restrict__ eu, const int32_t *__restrict__ ev,
+                          const int32_t *__restrict__ eslot,
+                          int32_t *tribuf, int32_t tricap, unsigned long long *cacc,
+                          unsigned long long *yacc, int32_t *status) {
+    const int lane = lane_id();
+    const int gw = global_warp();
+    int32_t *buf = tribuf + (int64_t)gw * tricap * 3;
+    for (int64_t k = gw; k < m; k += num_warps()) {
+        int32_t u = eu[k], v = ev[k], p = eslot[k];
+        int32_t bu = rp[u], du = rp[u + 1] - bu, bv = rp[v], dv = rp[v + 1] - bv;
+        // Tri_e in ascending order (scan N(u), test membership in N(v))
+        int32_t cnt = 0;
+        for (int32_t i0 = 0; i0 < du; i0 += WARP) {
+            int32_t i = i0 + lane;
+            bool keep = false;
+            int32_t x = 0;
+            if (i < du) { x = ldg(ci + bu + i); keep = find_in(ci + bv, dv, x) >= 0; }
+            unsigned mask = __ballot_sync(0xffffffffu, keep);
+            int32_t pos = cnt + __popc(mask & ((1u << lane) - 1));
+            if (keep) {
+                if (pos < tricap) buf[pos] = x; else atomicOr(status, ERR_CAPACITY);
+            }
+            cnt += __popc(mask);
+        }
+        __syncwarp();
+        if (cnt > tricap) cnt = tricap;
+        // CliqueCount
+        unsigned long long cl = 0;
+        for (int32_t i = 0; i < cnt; i++) {
+            int32_t w = buf[i];
+            int32_t bw = rp[w], dw = rp[w + 1] - bw;
+            for (int32_t j = lane; j < dw; j += WARP) cl += find_in(buf, cnt, ldg(ci + bw + j)) >= 0;
+        }
+        cl = warp_sum(cl);
+        // CycleCount over Star_u = N(u) \ {v} \ N(v)
+        unsigned long long cy = 0;
+        for (int32_t i = 0; i < du; i++) {
+            int32_t w = ldg(ci + bu + i);
+            if (w == v || find_in(ci + bv, dv, w) >= 0) continue;
+            int32_t bw = rp[w], dw = rp[w + 1] - bw;
+            for (int32_t j = lane; j < dw; j += WARP) {
+                int32_t r = ldg(ci + bw + j);
+                // r in Star_v: r in N(v), r != u, r not in N(u)
+                if (r != u && find_in(ci + bv, dv, r) >= 0 && find_in(ci + bu, du, r) < 0) cy++;
+            }
+        }
+        cy = warp_sum(cy);
+        if (lane == 0) { cacc[p] = cl >> 1; yacc[p] = cy; }
+        __syncwarp();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Steps 3-4 per edge: restricted counts from the identities, per-edge
+// columns (Corollaries 1-14) and the 13 sums of Algorithm 2.
+//
+// With s = T + cliq etc. (all per edge e = (u,v)):
+//   N_TSu1 = A_u - T - 2cliq                 (edges Tri-Star_u)
+//   N_SuSu1 = t(u) - T - cliq - N_TSu1       (edges inside Star_u)
+//   N_TI1  = D_T - 2T - 2cliq - N_TS1
+//   cyc    = C4(e) - N_TS1 - 2cliq           (oriented variant)
+//   N_SuI1 = (S1(u) - d_v - D_T - Su) - N_TSu1 - 2N_SuSu1 - cyc
+//   N_II1  = |E| - (du-1) - (dv-1) - 1 - (all edges touching the egonet)
+// ---------------------------------------------------------------------------
+struct FinalArgs {
+    int64_t m;
+    int32_t n;
+    int variant;              // 1 literal, 2 oriented
+    int per_edge;             // write columns
+    int need_restricted;      // per-edge restricted counts available
+    const int32_t *rp, *eu, *ev, *eslot, *mate;
+    const uint32_t *tslot;
+    const uint64_t *tnode, *s1, *au, *av, *dt;
+    const unsigned long long *cacc, *yacc;
+    uint64_t *out;
+    unsigned long long *sums;
+    int32_t *status;
+};
+
+__global__ void k_final(FinalArgs a) {
+    __shared__ unsigned long long red[S_NUM + X_NUM][8];
+    unsigned long long loc[S_NUM + X_NUM];
+    for (int i = 0; i < S_NUM + X_NUM; i++) loc[i] = 0;
+    int bad = 0;
+    const int64_t nn = a.n, mm = a.m;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < a.m; k += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t u = a.eu[k], v = a.ev[k], p = a.eslot[k];
+        const int64_t du = a.rp[u + 1] - a.rp[u], dv = a.rp[v + 1] - a.rp[v];
+        const int64_t T = a.tslot[p];
+        const int64_t Su = du - 1 - T, Sv = dv - 1 - T;
+        const int64_t I = nn - du - dv + T;
+        const int64_t II = mm - du - dv + 1;      // |E| - (du-1) - (dv-1) - 1
+        loc[S_T] += T; loc[S_S] += Su + Sv; loc[S_I] += I;
+        loc[S_TT] += T * (T - 1) / 2;
+        loc[S_SUSV] += Su * Sv;
+        loc[S_TS] += T * (Su + Sv);
+        loc[S_SS] += Su * (Su - 1) / 2 + Sv * (Sv - 1) / 2;
+        loc[S_TI] += T * I;
+        loc[S_SI] += (Su + Sv) * I;
+        loc[S_II] += (uint64_t)I * (uint64_t)(I - 1) / 2;
+        loc[S_II1] += II;
+        loc[X_T2 + S_NUM] += T * T;
+        int64_t cliq = 0, cyc = 0, c4 = 0;
+        if (a.variant == GD_VARIANT_LITERAL) {
+            cliq = (int64_t)a.cacc[p];
+            cyc = (int64_t)a.yacc[p];
+        } else {
+            const int32_t q = a.mate[p];
+            cliq = (int64_t)(a.cacc[p] + a.cacc[q]);
+            c4 = (int64_t)(a.yacc[p] + a.yacc[q]);
+            loc[X_C4 + S_NUM] += c4;
+        }
+        loc[S_CLIQ] += cliq;
+        if (!a.need_restricted) {
+            loc[S_CYC] += cyc;
+            continue;
+        }
+        const int64_t tsu = (int64_t)a.au[k] - T - 2 * cliq;
+        const int64_t tsv = (int64_t)a.av[k] - T - 2 * cliq;
+        const int64_t ts = tsu + tsv;
+        if (a.variant != GD_VARIANT_LITERAL) cyc = c4 - ts - 2 * cliq;
+        loc[S_CYC] += cyc;
+        const int64_t susu = (int64_t)a.tnode[u] - T - cliq - tsu;
+        const int64_t svsv = (int64_t)a.tnode[v] - T - cliq - tsv;
+        const int64_t DT = (int64_t)a.dt[k];
+        const int64_t ti = DT - 2 * T - 2 * cliq - ts;
+        const int64_t sui = ((int64_t)a.s1[u] - dv - DT - Su) - tsu - 2 * susu - cyc;
+        const int64_t svi = ((int64_t)a.s1[v] - du - DT - Sv) - tsv - 2 * svsv - cyc;
+        const int64_t ii1 = II - (cliq + ts + ti + susu + svsv + cyc + sui + svi);
+        if ((Su | Sv | I | tsu | tsv | susu | svsv | ti | cyc | sui | svi | ii1 | cliq) < 0) bad = 1;
+        if (a.per_edge) {
+            const int64_t ss = susu + svsv, si = sui + svi;
+            uint64_t *o = a.out + k * 15;
+            o[0] = T;
+            o[1] = Su + Sv;
+            o[2] = I;
+            o[3] = 0;
+            o[4] = cliq;
+            o[5] = T * (T - 1) / 2 - cliq + ts;
+            o[6] = T * (Su + Sv) - ts + ti + ss;
+            o[7] = cyc;
+            o[8] = Su * (Su - 1) / 2 + Sv * (Sv - 1) / 2 - ss;
+            o[9] = Su * Sv - cyc + si;
+            o[10] = T * I - ti;
+            o[11] = (Su + Sv) * I - si;
+            o[12] = ii1;
+            o[13] = (uint64_t)I * (uint64_t)(I - 1) / 2 - (uint64_t)ii1;
+            o[14] = 0;
+        }
+    }
+    if (bad) atomicOr(a.status, ERR_NEGATIVE);
+    // block reduction -> u128 atomics
+    const int lane = lane_id(), warp = threadIdx.x >> 5;
+    for (int i = 0; i < S_NUM + X_NUM; i++) {
+        unsigned long long x = warp_sum(loc[i]);
+        if (lane == 0) red[i][warp] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x < S_NUM + X_NUM) {
+        unsigned long long s = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) s += red[threadIdx.x][w];
+        add_u128(a.sums + 2 * threadIdx.x, s);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Step 4: completion (one thread), exact u128.
+// ---------------------------------------------------------------------------
+typedef unsigned __int128 u128;
+
+__device__ __forceinline__ u128 ld128(const unsigned long long *p) {
+    return (u128)p[0] | ((u128)p[1] << 64);
+}
+__device__ __forceinline__ void st128(unsigned long long *p, u128 x) {
+    p[0] = (unsigned long long)x; p[1] = (unsigned long long)(x >> 64);
+}
+
+__global__ void k_complete(const unsigned long long *sums, int64_t n, int derive_cyc,
+                           unsigned long long *result, int32_t *status) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    u128 s[S_NUM + X_NUM];
+    for (int i = 0; i < S_NUM + X_NUM; i++) s[i] = ld128(sums + 2 * i);
+    int err = 0;
+    // sum cyc_e from 4-cycle credits when per-edge restricted counts were
+    // not formed: sum_e N_TS1 = 2 sum T^2 - 2 sum T - 4 sum cliq, so
+    // sum cyc = sum C4(e) - sum N_TS1 - 2 sum cliq.
+    u128 scyc = s[S_CYC];
+    if (derive_cyc) {
+        u128 plus = s[S_NUM + X_C4] + 2 * s[S_T] + 2 * s[S_CLIQ];
+        u128 minus = 2 * s[S_NUM + X_T2];
+        if (minus > plus) err |= ERR_NEGATIVE;
+        scyc = plus - minus;
+    }
+    const u128 N = (u128)n;
+    const u128 C3 = N < 3 ? 0 : N * (N - 1) / 2 * (N - 2) / 3;
+    const u128 C4 = N < 4 ? 0 : N * (N - 1) / 2 * (N - 2) / 3 * (N - 3) / 4;
+    u128 f[15];
+    auto exdiv = [&](u128 a, unsigned d) -> u128 { if (a % d) err |= ERR_REMAINDER; return a / d; };
+    auto sub = [&](u128 a, u128 b) -> u128 { if (b > a) err |= ERR_NEGATIVE; return a - b; };
+    f[0] = exdiv(s[S_T], 3);                        // Eq. triangle
+    f[1] = exdiv(s[S_S], 2);                        // Eq. 2-star
+    f[2] = s[S_I];                                  // Eq. g3_3
+    f[3] = sub(C3, f[0] + f[1] + f[2]);             // Eq. g3_4
+    const u128 f41 = exdiv(s[S_CLIQ], 6);           // Lemma 1 (each 4-clique on 6 edges)
+    const u128 f44 = exdiv(scyc, 4);                // Lemma 2 (each 4-cycle on 4 edges)
+    const u128 f42 = sub(s[S_TT], 6 * f41);         // Lemma 1
+    const u128 f46 = sub(s[S_SUSV], 4 * f44);       // Lemma 2
+    const u128 f43 = exdiv(sub(s[S_TS], 4 * f42), 2);       // Lemma 3
+    const u128 f45 = exdiv(sub(s[S_SS], f43), 3);           // Lemma 4
+    const u128 f47 = exdiv(sub(s[S_TI], f43), 3);           // Lemma 5
+    const u128 f48 = exdiv(sub(s[S_SI], 2 * f46), 2);       // Lemma 6
+    const u128 f49 = exdiv(sub(s[S_II1], 6 * f41 + 4 * f42 + 2 * f43 + 4 * f44 + 2 * f46), 2);  // Eq. g4_9
+    const u128 f410 = sub(s[S_II], 2 * f49);                 // Lemma 7
+    const u128 f411 = sub(C4, f41 + f42 + f43 + f44 + f45 + f46 + f47 + f48 + f49 + f410);  // Eq. g4_11
+    f[4] = f41; f[5] = f42; f[6] = f43; f[7] = f44; f[8] = f45; f[9] = f46;
+    f[10] = f47; f[11] = f48; f[12] = f49; f[13] = f410; f[14] = f411;
+    for (int i = 0; i < 15; i++) st128(result + 2 * i, f[i]);
+    if (err) atomicOr(status, err);
+}
+
+inline unsigned grid_for(int64_t items, int per_block, int max_blocks) {
+    int64_t b = (items + per_block - 1) / per_block;
+    if (b < 1) b = 1;
+    if (b > max_blocks) b = max_blocks;
+    return (unsigned)b;
+}
+
+}  // namespace
+
+// ===========================================================================
+// host launchers (all asynchronous on the graph's stream)
+// ===========================================================================
+
+static int sm_count(gd_graph *g) { return g->ctx->num_sms > 0 ? g->ctx->num_sms : 152; }
+
+__global__ void k_max_degree(int32_t n, const int32_t *__restrict__ rp, int32_t *out) {
+    int32_t best = 0;
+    for (int32_t u = blockIdx.x * blockDim.x + threadIdx.x; u < n; u += gridDim.x * blockDim.x)
+        best = max(best, rp[u + 1] - rp[u]);
+    for (int o = 16; o > 0; o >>= 1) best = max(best, __shfl_xor_sync(0xffffffffu, best, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out, best);
+}
+
+cudaError_t max_degree(gd_graph *g, int32_t *out_host) {
+    Workspace &w = g->ws;
+    cudaStream_t st = g->stream;
+    cudaError_t e = cudaMemsetAsync(w.status + 3, 0, sizeof(int32_t), st);
+    if (e) return e;
+    if (g->n > 0) k_max_degree<<<grid_for(g->n, 256, sm_count(g) * 8), 256, 0, st>>>(g->n, g->rp, w.status + 3);
+    e = cudaMemcpyAsync(out_host, w.status + 3, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+    if (e) return e;
+    e = cudaStreamSynchronize(st);
+    if (e) return e;
+    return cudaMemsetAsync(w.status + 3, 0, sizeof(int32_t), st);
+}
+
+cudaError_t validate_csr(gd_graph *g, int32_t *bad_index, int32_t *bad_code) {
+    Workspace &w = g->ws;
+    cudaStream_t st = g->stream;
+    int32_t init[4] = {0, 0x7fffffff, 0, 0};
+    cudaError_t e = cudaMemcpyAsync(w.status, init, sizeof(init), cudaMemcpyHostToDevice, st);
+    if (e) return e;
+    if (g->n > 0) k_validate<<<grid_for(g->n, 256, sm_count(g) * 8), 256, 0, st>>>(g->n, g->nnz, g->rp, g->ci, w.status);
+    int32_t h[4];
+    e = cudaMemcpyAsync(h, w.status, sizeof(h), cudaMemcpyDeviceToHost, st);
+    if (e) return e;
+    e = cudaStreamSynchronize(st);
+    if (e) return e;
+    *bad_code = h[0];
+    *bad_index = h[1];
+    return cudaMemsetAsync(w.status, 0, 4 * sizeof(int32_t), st);
+}
+
+// Step 1 and the schedule: edge list, reverse slots, |Tri_e| per slot, wedge
+// tiers.  Everything is recomputed from the CSR on every count call.
+cudaError_t prepare_edges(gd_graph *g) {
+    Workspace &w = g->ws;
+    cudaStream_t st = g->stream;
+    const int sms = sm_count(g);
+    const int32_t n = g->n;
+    cudaError_t e = cudaMemsetAsync(w.status, 0, 4 * sizeof(int32_t), st);
+    if (e) return e;
+    if (n == 0) return cudaSuccess;
+    int64_t *cnt = w.scan_tmp;
+    int64_t *offs = w.scan_tmp + (n + 1);
+    int64_t *tmp = w.scan_tmp + 2 * (int64_t)(n + 1);
+    k_upper_count<<<grid_for(n, 256, sms * 8), 256, 0, st>>>(n, g->rp, g->ci, w.first_up, cnt);
+    e = exclusive_scan(cnt, offs, n, tmp, st);
+    if (e) return e;
+    k_narrow<<<grid_for(n + 1, 256, sms * 8), 256, 0, st>>>(offs, w.eoff, n + 1);
+    k_edge_list<<<grid_for((int64_t)n * 32, 256, sms * 8), 256, 0, st>>>(n, g->rp, g->ci, w.first_up, w.eoff,
+                                                                         w.eu, w.ev, w.eslot);
+    if (g->m > 0) {
+        k_mate<<<grid_for(g->m, 256, sms * 8), 256, 0, st>>>(g->m, g->rp, g->ci, w.eu, w.ev, w.eslot, w.mate);
+        k_triangles<<<grid_for(g->m * 32, 256, sms * 16), 256, 0, st>>>(g->m, g->rp, g->ci, w.eu, w.ev, w.eslot,
+                                                                        w.mate, w.tslot);
+    }
+    e = cudaMemsetAsync(w.counters, 0, 8 * sizeof(int32_t), st);
+    if (e) return e;
+    const int32_t cap = g->ctx->opt.smem_table_max;
+    k_wedge_estimate<<<grid_for((int64_t)n * 32, 256, sms * 16), 256, 0, st>>>(n, g->rp, g->ci, cap / 2,
+                                                                              w.vlist, w.counters);
+    return cudaGetLastError();
+}
+
+cudaError_t run_per_edge_sums(gd_graph *g) {
+    Workspace &w = g->ws;
+    cudaStream_t st = g->stream;
+    const int sms = sm_count(g);
+    if (g->n > 0)
+        k_node<<<grid_for((int64_t)g->n * 32, 256, sms * 16), 256, 0, st>>>(g->n, g->rp, g->ci, w.tslot, w.tnode, w.s1);
+    if (g->m > 0)
+        k_tri_sums<<<grid_for(g->m * 32, 256, sms * 16), 256, 0, st>>>(g->m, g->rp, g->ci, w.eu, w.ev, w.tslot,
+                                                                       w.au, w.av, w.dt);
+    return cudaGetLastError();
+}
+
+static const int TRI_THREADS = 256;
+int32_t tribuf_warps(int sms) { return sms * 8 * (TRI_THREADS / 32); }
+
+size_t cycle_smem_bytes(int32_t cap) { return (size_t)cap * 8 + (size_t)(cap / 2) * 4; }
+
+cudaError_t run_cliques_cycles(gd_graph *g, int variant) {
+    Workspace &w = g->ws;
+    cudaStream_t st = g->stream;
+    const int sms = sm_count(g);
+    cudaError_t e;
+    if (g->m == 0) return cudaSuccess;
+    e = cudaMemsetAsync(w.cacc, 0, sizeof(uint64_t) * g->nnz, st);
+    if (e) return e;
+    e = cudaMemsetAsync(w.yacc, 0, sizeof(uint64_t) * g->nnz, st);
+    if (e) return e;
+    const int32_t warps = tribuf_warps(sms);
+    const int32_t tricap = (int32_t)(w.tribuf_words / ((int64_t)warps * 3));
+    const unsigned tri_blocks = (unsigned)(warps / (TRI_THREADS / 32));
+    if (variant == GD_VARIANT_LITERAL) {
+        k_literal<<<tri_blocks, TRI_THREADS, 0, st>>>(g->m, g->rp, g->ci, w.eu, w.ev, w.eslot, w.tribuf, tricap,
+                                                      (unsigned long long *)w.cacc, (unsigned long long *)w.yacc,
+                                                      w.status);
+        return cudaGetLastError();
+    }
+    k_cliques_oriented<<<tri_blocks, TRI_THREADS, 0, st>>>(g->m, g->rp, g->ci, w.eu, w.ev, w.eslot, w.mate,
+                                                           w.tribuf, tricap, (unsigned long long *)w.cacc, w.status);
+    const int32_t cap = g->ctx->opt.smem_table_max;
+    const size_t smem = cycle_smem_bytes(cap);
+    e = cudaFuncSetAttribute(k_cycles_oriented<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e) return e;
+    k_cycles_oriented<false><<<(unsigned)(sms * 2), 256, smem, st>>>(
+        g->n, g->rp, g->ci, w.vlist, w.counters, (uint32_t)(cap - 1), nullptr, (unsigned long long *)w.yacc);
+    k_cycles_oriented<true><<<(unsigned)w.wtab_ctas, 256, 0, st>>>(
+        g->n, g->rp, g->ci, w.vlist, w.counters, 0, w.wtab, (unsigned long long *)w.yacc);
+    return cudaGetLastError();
+}
+
+cudaError_t run_final(gd_graph *g, int variant, bool per_edge, uint64_t *out_dev) {
+    Workspace &w = g->ws;
+    cudaStream_t st = g->stream;
+    const int sms = sm_count(g);
+    cudaError_t e = cudaMemsetAsync(w.sums, 0, sizeof(unsigned long long) * 2 * (S_NUM + X_NUM), st);
+    if (e) return e;
+    if (g->m == 0) return cudaSuccess;
+    FinalArgs a;
+    a.m = g->m; a.n = g->n; a.variant = variant; a.per_edge = per_edge ? 1 : 0;
+    a.need_restricted = per_edge ? 1 : 0;
+    a.rp = g->rp; a.eu = w.eu; a.ev = w.ev; a.eslot = w.eslot; a.mate = w.mate; a.tslot = w.tslot;
+    a.tnode = w.tnode; a.s1 = w.s1; a.au = w.au; a.av = w.av; a.dt = w.dt;
+    a.cacc = (const unsigned long long *)w.cacc; a.yacc = (const unsigned long long *)w.yacc;
+    a.out = out_dev; a.sums = w.sums; a.status = w.status;
+    k_final<<<grid_for(g->m, 256, sms * 8), 256, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+// derive_cyc: sum cyc_e is derived from the 4-cycle credits (oriented
+// variant without per-edge restricted counts).
+cudaError_t run_complete(gd_graph *g, int derive_cyc) {
+    k_complete<<<1, 32, 0, g->stream>>>(g->ws.sums, g->n, derive_cyc, g->ws.result, g->ws.status);
+    return cudaGetLastError();
+}
+
+}  // namespace gdi

@@ -1,0 +1,126 @@
+// gd_internal.h -- shared between the host API (gd_api.cu) and the kernel
+// translation units.  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stddef.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/gd.h"
+
+namespace gdi {
+
+// Indices of the 13 edge-summed quantities of Algorithm 2 (Steps 1-3).
+enum SumIdx {
+    S_T = 0,     // sum |Tri_e|
+    S_S,         // sum |Star_u| + |Star_v|
+    S_I,         // sum |V| - |N(u) u N(v)|
+    S_CLIQ,      // sum cliq_e  (= 6 f41)
+    S_CYC,       // sum cyc_e   (= 4 f44)
+    S_TT,        // sum C(T,2)
+    S_SUSV,      // sum Su*Sv
+    S_TS,        // sum T(Su+Sv)
+    S_SS,        // sum C(Su,2)+C(Sv,2)
+    S_TI,        // sum T*I
+    S_SI,        // sum (Su+Sv)*I
+    S_II,        // sum C(I,2)
+    S_II1,       // sum |E| - du - dv + 1
+    S_NUM
+};
+
+// Extra sums used only to derive sum cyc_e in the global path.
+enum ExtraIdx { X_T2 = 0, X_C4 = 1, X_NUM = 2 };
+
+// Device-side error bits (gdi::Status word).
+enum ErrBits {
+    ERR_NEGATIVE = 1,     // a restricted count came out negative: inconsistent input
+    ERR_REMAINDER = 2,    // an exact division left a remainder
+    ERR_CAPACITY = 4,     // a work buffer was too small (host sizing bug)
+    ERR_CSR = 8,          // CSR validation failed
+    ERR_TIMEOUT = 16      // a bounded wait gave up
+};
+
+// Per-graph device scratch for the wedge tables and triangle buffers.
+struct Workspace {
+    // edge list (canonical order: row u ascending, v > u ascending)
+    int32_t *first_up = nullptr;   // [n]   first slot of row u with col > u
+    int32_t *eoff = nullptr;       // [n+1] edge offset of row u
+    int32_t *eu = nullptr, *ev = nullptr, *eslot = nullptr;   // [m]
+    int32_t *mate = nullptr;       // [nnz] slot of the reverse direction
+    uint32_t *tslot = nullptr;     // [nnz] |Tri| of the edge of each slot
+    // per-edge mode
+    uint64_t *tnode = nullptr;     // [n] edges inside N(x)
+    uint64_t *s1 = nullptr;        // [n] sum of neighbour degrees
+    uint64_t *au = nullptr, *av = nullptr, *dt = nullptr;   // [m]
+    uint64_t *cacc = nullptr;      // [nnz] 4-clique credits per slot
+    uint64_t *yacc = nullptr;      // [nnz] 4-cycle credits per slot (or cyc_e for literal)
+    // schedule
+    int32_t *vlist = nullptr;      // [n] vertices with wedges, small tier then big tier
+    int32_t *counters = nullptr;   // [8] small counters (list sizes, max d+)
+    // scratch
+    int32_t *tribuf = nullptr;     // [warps * tricap * 3]
+    int64_t tribuf_words = 0;
+    uint32_t *wtab = nullptr;      // [big_ctas * n] dense wedge tables (zero at rest)
+    int32_t wtab_ctas = 0;
+    // results
+    unsigned long long *sums = nullptr;   // [2*(S_NUM+X_NUM)] u128 as lo,hi
+    unsigned long long *result = nullptr; // [30] 15 x u128
+    int32_t *status = nullptr;            // [4] error bits, detail
+    // scan scratch
+    int64_t *scan_tmp = nullptr;
+    // per-edge output staging when the caller's buffer is on the host
+    uint64_t *out_buf = nullptr;
+    size_t out_buf_bytes = 0;
+    size_t bytes = 0;
+};
+
+}  // namespace gdi
+
+struct gd_ctx {
+    int device = 0;
+    size_t budget = 0;           // 0 = unlimited
+    size_t in_use = 0;           // device bytes held by this context's graphs
+    gd_options opt{};
+    std::string err;
+    int num_sms = 0;
+    cudaStream_t stream = nullptr;   // for batch calls
+    std::vector<gd_graph *> graphs;
+    // batch scratch (grown on demand)
+    void *batch_buf = nullptr;
+    size_t batch_bytes = 0;
+};
+
+struct gd_graph {
+    gd_ctx *ctx = nullptr;
+    int32_t n = 0;
+    int64_t nnz = 0, m = 0;
+    cudaStream_t stream = nullptr;
+    int32_t *rp = nullptr, *ci = nullptr;
+    bool borrowed = false;
+    size_t csr_bytes = 0;
+    int32_t max_deg = 0;
+    bool prepared = false;       // edge list / mate / T computed
+    bool per_edge_ready = false; // per-edge arrays allocated
+    gdi::Workspace ws;
+};
+
+namespace gdi {
+
+// kernels (gd_count.cu)
+cudaError_t validate_csr(gd_graph *g, int32_t *bad_index_host, int32_t *bad_code_host);
+cudaError_t prepare_edges(gd_graph *g);                   // edge list, mate, T per slot
+cudaError_t run_per_edge_sums(gd_graph *g);               // t(x), S1(x), A_u, A_v, D_T
+cudaError_t run_cliques_cycles(gd_graph *g, int variant); // cacc, yacc
+cudaError_t run_final(gd_graph *g, int variant, bool per_edge, uint64_t *out_dev);
+cudaError_t run_complete(gd_graph *g, int derive_cyc);
+cudaError_t max_degree(gd_graph *g, int32_t *out_host);
+int32_t tribuf_warps(int sms);
+
+// batch (gd_batch.cu)
+int batch_count(gd_ctx *ctx, int32_t num_graphs, const int32_t *gnp, const int32_t *rp,
+                const int32_t *ci, int64_t nnz, int32_t ntot, uint64_t *out_dev);
+
+}  // namespace gdi

@@ -1,0 +1,319 @@
+"""Python binding of libgd (include/gd.h): argument marshalling only.
+
+Every count runs in the CUDA kernels of ``libgd.so``; nothing here computes
+graphlet counts.  If the library is not built, every call raises -- there is no
+CPU fallback.
+
+Two layers:
+
+* functions with the C names (``gd_init``, ``gd_create_csr``, ``gd_count_global``,
+  ``gd_count_per_edge``, ``gd_count_batch``, ...) taking handles and raw pointers;
+* ``Context`` / ``Graph`` wrappers that accept numpy arrays (host memory) or torch
+  tensors (device memory, via ``data_ptr()``) and torch streams.
+
+Counts come back in Table 1 order [g31 g32 g33 g34 g41 ... g4_10 g4_11].
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+import threading
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libgd.so")
+HEADER = os.path.join(HERE, "..", "include", "gd.h")
+
+GRAPHLETS = ["g31", "g32", "g33", "g34", "g41", "g42", "g43", "g44", "g45", "g46",
+             "g47", "g48", "g49", "g4_10", "g4_11"]
+
+GD_OK, GD_EINVAL, GD_ENOMEM, GD_ECUDA, GD_EAGAIN, GD_ETIMEDOUT, GD_EOVERFLOW, GD_ENOTIMPL, GD_EARITH = range(9)
+STATUS_NAMES = {0: "GD_OK", 1: "GD_EINVAL", 2: "GD_ENOMEM", 3: "GD_ECUDA", 4: "GD_EAGAIN",
+                5: "GD_ETIMEDOUT", 6: "GD_EOVERFLOW", 7: "GD_ENOTIMPL", 8: "GD_EARITH"}
+GD_DEVICE_PTRS, GD_VALIDATE, GD_BORROW = 1, 2, 4
+GD_OUT_DEVICE = 1
+GD_VARIANT_AUTO, GD_VARIANT_LITERAL, GD_VARIANT_ORIENTED = 0, 1, 2
+
+
+class GDError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class gd_u128(ctypes.Structure):
+    _fields_ = [("lo", ctypes.c_uint64), ("hi", ctypes.c_uint64)]
+
+
+class gd_options(ctypes.Structure):
+    _fields_ = [("variant", ctypes.c_int32), ("block_threads", ctypes.c_int32),
+                ("ctas_per_sm", ctypes.c_int32), ("smem_table_max", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 8)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def load():
+    """Load libgd.so; raises if it has not been built (no fallback)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libgd.so is not built; run paper_1506_04322_gb300.build.build() "
+                               "(nvcc for sm_103a) -- there is no CPU fallback")
+        lib = ctypes.CDLL(LIB_PATH)
+        vp, i32, i64, sz = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t
+        sig = {
+            "gd_default_options": (None, [vp]),
+            "gd_init": (ctypes.c_int, [ctypes.POINTER(vp), ctypes.c_int, sz, vp]),
+            "gd_destroy": (None, [vp]),
+            "gd_last_error": (ctypes.c_char_p, [vp]),
+            "gd_create_csr": (ctypes.c_int, [vp, i32, i64, vp, vp, ctypes.c_int, vp, ctypes.POINTER(vp)]),
+            "gd_graph_info": (ctypes.c_int, [vp, ctypes.POINTER(i32), ctypes.POINTER(i64)]),
+            "gd_graph_footprint": (ctypes.c_int, [vp, ctypes.POINTER(sz)]),
+            "gd_destroy_graph": (None, [vp]),
+            "gd_count_global": (ctypes.c_int, [vp, vp]),
+            "gd_count_per_edge": (ctypes.c_int, [vp, vp, ctypes.c_int, vp]),
+            "gd_count_batch": (ctypes.c_int, [vp, i32, vp, vp, vp, ctypes.c_int, vp]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = lib
+        return lib
+
+
+def declared_symbols() -> list[str]:
+    """Function names declared in include/gd.h."""
+    with open(HEADER) as f:
+        text = f.read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(gd_[a-z0-9_]+)\s*\(", text)))
+
+
+# ---------------------------------------------------------------------------
+# C-named thin wrappers
+# ---------------------------------------------------------------------------
+
+def _u128_list(arr) -> list[int]:
+    return [int(x.lo) | (int(x.hi) << 64) for x in arr]
+
+
+def gd_default_options() -> gd_options:
+    o = gd_options()
+    load().gd_default_options(ctypes.byref(o))
+    return o
+
+
+def gd_init(device: int = 0, hbm_budget_bytes: int = 0, options: gd_options | None = None):
+    h = ctypes.c_void_p()
+    rc = load().gd_init(ctypes.byref(h), device, hbm_budget_bytes,
+                        ctypes.byref(options) if options is not None else None)
+    if rc:
+        raise GDError(rc, "gd_init failed")
+    return h
+
+
+def gd_destroy(ctx) -> None:
+    load().gd_destroy(ctx)
+
+
+def gd_last_error(ctx) -> str:
+    s = load().gd_last_error(ctx)
+    return s.decode() if s else ""
+
+
+def _check(ctx, rc, what):
+    if rc:
+        raise GDError(rc, f"{what}: {gd_last_error(ctx)}")
+
+
+def gd_create_csr(ctx, n: int, nnz: int, row_ptr: int, col_idx: int, flags: int = 0, stream: int = 0):
+    h = ctypes.c_void_p()
+    rc = load().gd_create_csr(ctx, n, nnz, row_ptr, col_idx, flags, stream or None, ctypes.byref(h))
+    _check(ctx, rc, "gd_create_csr")
+    return h
+
+
+def gd_destroy_graph(graph) -> None:
+    load().gd_destroy_graph(graph)
+
+
+def gd_graph_info(graph) -> tuple[int, int]:
+    n, m = ctypes.c_int32(), ctypes.c_int64()
+    load().gd_graph_info(graph, ctypes.byref(n), ctypes.byref(m))
+    return n.value, m.value
+
+
+def gd_graph_footprint(graph) -> int:
+    b = ctypes.c_size_t()
+    load().gd_graph_footprint(graph, ctypes.byref(b))
+    return b.value
+
+
+def gd_count_global(ctx, graph) -> list[int]:
+    out = (gd_u128 * 15)()
+    _check(ctx, load().gd_count_global(graph, out), "gd_count_global")
+    return _u128_list(out)
+
+
+def gd_count_per_edge(ctx, graph, out_ptr: int, out_flags: int = 0, want_global: bool = True):
+    glob = (gd_u128 * 15)() if want_global else None
+    _check(ctx, load().gd_count_per_edge(graph, out_ptr, out_flags, glob), "gd_count_per_edge")
+    return _u128_list(glob) if want_global else None
+
+
+def gd_count_batch(ctx, num_graphs: int, graph_node_ptr: int, row_ptr: int, col_idx: int,
+                   flags: int, out_ptr: int) -> None:
+    _check(ctx, load().gd_count_batch(ctx, num_graphs, graph_node_ptr, row_ptr, col_idx, flags, out_ptr),
+           "gd_count_batch")
+
+
+# ---------------------------------------------------------------------------
+# object layer
+# ---------------------------------------------------------------------------
+
+def _ptr(a):
+    """(pointer, is_device) of a numpy array or a torch tensor."""
+    if isinstance(a, np.ndarray):
+        if not a.flags.c_contiguous:
+            raise ValueError("array must be contiguous")
+        return a.ctypes.data, False
+    if hasattr(a, "data_ptr") and hasattr(a, "is_cuda"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr(), bool(a.is_cuda)
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def _torch_stream():
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream().cuda_stream
+    except ImportError:
+        pass
+    return 0
+
+
+class Context:
+    """A libgd context on one GPU."""
+
+    def __init__(self, device: int = 0, hbm_budget_bytes: int = 0, variant: int = GD_VARIANT_AUTO,
+                 smem_table_max: int | None = None):
+        o = gd_default_options()
+        o.variant = variant
+        if smem_table_max:
+            o.smem_table_max = smem_table_max
+        self.handle = gd_init(device, hbm_budget_bytes, o)
+        self._graphs = []
+
+    def close(self):
+        if self.handle:
+            gd_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def last_error(self) -> str:
+        return gd_last_error(self.handle)
+
+    def graph(self, row_ptr, col_idx=None, n: int | None = None, validate: bool = False,
+              borrow: bool = False, stream: int | None = None) -> "Graph":
+        """Upload a CSR graph: numpy arrays, torch tensors, or an object with
+        ``row_ptr``/``col_idx``/``n`` attributes (inputs.Graph)."""
+        if col_idx is None:
+            g = row_ptr
+            row_ptr, col_idx, n = g.row_ptr, g.col_idx, g.n
+        if n is None:
+            n = int(row_ptr.shape[0]) - 1
+        nnz = int(col_idx.shape[0])
+        if isinstance(row_ptr, np.ndarray):
+            row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int32)
+            col_idx = np.ascontiguousarray(col_idx, dtype=np.int32)
+            if col_idx.size == 0:
+                col_idx = np.zeros(1, dtype=np.int32)
+        keep = [row_ptr, col_idx]
+        rp, dev = _ptr(row_ptr)
+        ci, dev2 = _ptr(col_idx)
+        if dev != dev2:
+            raise ValueError("row_ptr and col_idx must both be on the host or both on the device")
+        flags = (GD_DEVICE_PTRS if dev else 0) | (GD_VALIDATE if validate else 0) | (GD_BORROW if borrow else 0)
+        st = _torch_stream() if stream is None else stream
+        h = gd_create_csr(self.handle, n, nnz, rp, ci, flags, st)
+        gr = Graph(self, h, keep if borrow else None)
+        return gr
+
+    def count_batch(self, batch, out=None, validate: bool = False, device_out: bool = False):
+        """Per-graph global counts of a packed batch (inputs.PackedBatch or
+        arrays/tensors graph_node_ptr, row_ptr, col_idx).  Returns a uint64
+        array [G, 15] (numpy, or the given/allocated torch tensor)."""
+        gnp, rp, ci = batch.graph_node_ptr, batch.row_ptr, batch.col_idx
+        G = int(gnp.shape[0]) - 1
+        pg, dev = _ptr(gnp)
+        pr, _ = _ptr(rp)
+        pc, _ = _ptr(ci if ci.shape[0] > 0 else (np.zeros(1, np.int32) if not dev else ci))
+        flags = (GD_DEVICE_PTRS if dev else 0) | (GD_VALIDATE if validate else 0)
+        if out is None:
+            if device_out:
+                import torch
+                out = torch.empty((max(G, 1), 15), dtype=torch.int64, device="cuda")
+            else:
+                out = np.zeros((max(G, 1), 15), dtype=np.uint64)
+        po, odev = _ptr(out)
+        if odev:
+            flags |= GD_OUT_DEVICE
+        gd_count_batch(self.handle, G, pg, pr, pc, flags, po)
+        return out[:G]
+
+
+class Graph:
+    def __init__(self, ctx: Context, handle, keep):
+        self.ctx = ctx
+        self.handle = handle
+        self._keep = keep
+        self.n, self.m = gd_graph_info(handle)
+
+    def close(self):
+        if self.handle and self.ctx.handle:
+            gd_destroy_graph(self.handle)
+        self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def footprint(self) -> int:
+        return gd_graph_footprint(self.handle)
+
+    def count_global(self) -> list[int]:
+        return gd_count_global(self.ctx.handle, self.handle)
+
+    def count_per_edge(self, out=None, want_global: bool = True):
+        """uint64 [m, 15] per-edge counts (numpy on the host, or into the given
+        torch CUDA tensor of shape [m, 15], dtype int64/uint64 bits).
+        Returns (per_edge, global_counts)."""
+        if out is None:
+            out = np.zeros((max(self.m, 1), 15), dtype=np.uint64)
+        po, dev = _ptr(out)
+        g = gd_count_per_edge(self.ctx.handle, self.handle, po, GD_OUT_DEVICE if dev else 0, want_global)
+        return out[:self.m], g
