@@ -1,0 +1,375 @@
+"""Benchmark: exact 3+4-node graphlet counts (global + per-edge) on one GB300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gd|reference]
+
+One step = the whole single-graph path of libgd on the Chung-Lu workload
+(n = 1,000,000, ~10M undirected edges, Pareto exponent 2.1, expected degree
+capped at 50,000, seed 2): CSR ingest/schedule, Step 1 (|Tri_e| per edge),
+node/triangle sums, Step 2 (4-cliques and 4-cycles), Step 3/4 per edge
+(15 columns written to HBM) and the exact u128 global completion.
+
+* ``value``  -- edges/s with the CSR resident in HBM (CUDA events on the
+  library's stream, L2 flushed by a 512 MB write between timed steps).
+* ``e2e``    -- the same metric through the C ABI with host buffers: upload the
+  CSR from pinned host memory, count, copy the per-edge matrix and the global
+  counts back to pinned host memory, release the graph.
+* ``roofline`` -- the dominant kernel's algorithmic bytes per launch over its
+  average CUDA-event duration (timed live in the timed region), against the
+  measured HBM copy bandwidth.
+* ``cpu_baseline`` -- the CPU oracle (per-edge records from the definitions,
+  single thread) on a random sample of the same graph's edges.
+
+Multi-GPU (torchrun): replicas only -- every rank counts its own copy of the
+workload (weak scaling); there is no collective on the data path.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1506_04322_gb300 import inputs  # noqa: E402
+
+METRIC = "edges/sec (exact 3+4-node graphlet counts)"
+UNIT = "edges/s"
+L2_FLUSH_BYTES = 512 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gd", choices=["gd", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.device)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, power, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(smax), "samples": len(sm),
+                "power_w_max": max(power) if power else None, "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------------------
+# algorithmic bytes (per kernel launch) from the CSR
+# ---------------------------------------------------------------------------
+
+def algorithmic_bytes(g) -> dict:
+    """Bytes each kernel's algorithm must move for this graph (4-byte ids,
+    8-byte counters), per launch.  Definitions:
+      step1  = sum_e [4(du+dv) + 32]      both lists of every edge + row bounds
+               (the marking pass of Algorithm 2, Step 1)
+      final  = per edge: 12 B edge list + 8 B slots + 4 B |Tri| + 32 B credits
+               + 24 B A_u/A_v/D_T + 32 B node sums + 16 B row bounds,
+               120 B of per-edge columns written
+      wedge  = sum over oriented wedges (u, v, y), v and y ranked below u, of
+               2 x (4 B id + 8 B row bounds of y) = 24 B per wedge visit
+    """
+    d = g.degrees().astype(np.int64)
+    e = g.edges()
+    du, dv = d[e[:, 0]], d[e[:, 1]]
+    m = len(e)
+    step1 = int((4 * (du + dv) + 32).sum())
+    wedges = int(np.minimum(du, dv).sum())   # sum_e d(lower-ranked endpoint)
+    return {
+        "k_triangles": step1,
+        "k_tri_sums": step1,
+        "k_final": m * (12 + 8 + 4 + 32 + 24 + 32 + 16 + 120),
+        "k_cycles_wedges": 24 * wedges,
+        "wedges": wedges,
+        "step1": step1,
+    }
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle baseline
+# ---------------------------------------------------------------------------
+
+def cpu_baseline(g, seconds: float, seed: int = 0) -> dict:
+    from oracle import oracle
+    e = g.edges()
+    rng = np.random.default_rng(seed)
+    order = rng.permutation(len(e))
+    done, t0 = 0, time.perf_counter()
+    chunk = 16
+    while time.perf_counter() - t0 < seconds and done < len(e):
+        idx = order[done:done + chunk]
+        oracle.edges_direct(g, e[idx])
+        done += len(idx)
+    dt = time.perf_counter() - t0
+    return {"value": done / dt, "unit": UNIT, "cores": 1, "kind": "oracle", "_edges": done, "_seconds": dt,
+            "sample": f"{done} uniformly random edges of the {g.m}-edge graph, per-edge counts from the "
+                      f"definitions (O1 record), one thread, {dt:.1f} s"}
+
+
+# ---------------------------------------------------------------------------
+# arms
+# ---------------------------------------------------------------------------
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    g = inputs.chung_lu_1m()
+    per_step = max(2.0, 60.0 / max(1, args.steps + args.warmup))
+    for i in range(args.warmup):
+        cpu_baseline(g, min(per_step, 2.0), seed=100 + i)
+    vals = [cpu_baseline(g, per_step, seed=i) for i in range(args.steps)]
+    total_edges = sum(v["_edges"] for v in vals)
+    total_t = sum(v["_seconds"] for v in vals)
+    value = total_edges / total_t
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * total_t / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+        "data": "synthetic", "config": {"workload": g.name, "n": g.n, "m": g.m},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{int(total_edges)} random edges per run, O1 per-edge records"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_gd(args):
+    import torch
+    from paper_1506_04322_gb300 import gd
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    device = local if ws > 1 else 0
+    torch.cuda.set_device(device)
+    g = inputs.chung_lu_1m()
+    m = g.m
+
+    ctx = gd.Context(device)
+    stream = torch.cuda.Stream(device=device)
+    rp = torch.from_numpy(g.row_ptr).to(device)
+    ci = torch.from_numpy(g.col_idx).to(device)
+    out = torch.empty((m, 15), dtype=torch.int64, device=device)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=device)
+    torch.cuda.synchronize()
+    h = ctx.graph(rp, ci, n=g.n, borrow=True, stream=stream.cuda_stream)
+
+    def step():
+        return h.count_per_edge(out=out)[1]
+
+    for _ in range(max(3, args.warmup)):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        glob = step()
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(device)
+    if rank == 0:
+        clocks.start()
+        time.sleep(0.3)
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    launches0 = ctx.kernel_launches()
+    ctx.profile_begin()
+    total_ms = 0.0
+    for _ in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()                       # L2 flush, outside the timed events
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+        glob2 = step()
+        with torch.cuda.stream(stream):
+            e1.record(stream)
+        e1.synchronize()
+        total_ms += e0.elapsed_time(e1)
+        if glob2 != glob:
+            raise RuntimeError("global counts changed between steps")
+    prof = ctx.profile_end()
+    launches = ctx.kernel_launches() - launches0
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop() if rank == 0 else None
+
+    ms = total_ms / args.steps
+    if ws > 1:
+        t = torch.tensor([ms], device=device, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    value = ws * m / (ms / 1000.0)
+
+    # end to end through the C ABI with pinned host buffers
+    rp_h = torch.from_numpy(g.row_ptr).pin_memory()
+    ci_h = torch.from_numpy(g.col_idx).pin_memory()
+    out_h = torch.empty((m, 15), dtype=torch.int64).pin_memory()
+    h2d = 4 * (g.n + 1) + 4 * g.nnz
+    d2h = 8 * 15 * m + 16 * 15
+
+    def e2e_step():
+        gh = gd.gd_create_csr(ctx.handle, g.n, g.nnz, rp_h.data_ptr(), ci_h.data_ptr(), 0, stream.cuda_stream)
+        try:
+            r = gd.gd_count_per_edge(ctx.handle, gh, out_h.data_ptr(), 0, True)
+        finally:
+            gd.gd_destroy_graph(gh)
+        return r
+
+    e2e_step()
+    e2e_steps = max(2, min(args.steps, 5))
+    if ws > 1:
+        torch.distributed.barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        r = e2e_step()
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    if r != glob:
+        raise RuntimeError("end-to-end counts differ from the device-resident counts")
+    if ws > 1:
+        t = torch.tensor([e2e_s], device=device, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t.item())
+
+    if rank != 0:
+        if ws > 1:
+            torch.distributed.destroy_process_group()
+        return
+
+    # roofline of the dominant kernel
+    ab = algorithmic_bytes(g)
+    peak, peak_kind = load_peaks()
+    kern = {k: {"ms_per_launch": v[0] / max(v[1], 1), "launches": v[1], "ms_total": v[0]} for k, v in prof.items()}
+    dom = max(kern, key=lambda k: kern[k]["ms_total"])
+    if dom in ab:
+        bytes_per_launch = ab[dom]
+    elif dom.startswith("k_cycles"):
+        bytes_per_launch = ab["k_cycles_wedges"]
+    else:
+        bytes_per_launch = None
+    roof = None
+    if bytes_per_launch:
+        achieved = bytes_per_launch / (kern[dom]["ms_per_launch"] / 1000.0) / 1e9
+        roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
+                "algorithmic_bytes_per_launch": bytes_per_launch}
+
+    cpu = None
+    if not args.no_cpu_baseline and ws == 1:
+        cpu = cpu_baseline(g, args.cpu_seconds)
+        cpu = {k: v for k, v in cpu.items() if not k.startswith("_")}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": g.name, "n": g.n, "m": g.m, "mode": "per-edge (15 columns) + global",
+                   "variant": "oriented", "seed": 2, "l2": "flushed between timed steps (512 MB write)",
+                   "parallelism": f"replicas x{ws}"},
+        "e2e": {"value": ws * m / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "clocks": clk,
+        "kernels": {k: round(v["ms_total"] / args.steps, 3) for k, v in sorted(kern.items(), key=lambda kv: -kv[1]["ms_total"])},
+        "global_counts": [str(x) for x in glob],
+    }
+    print(json.dumps(line), flush=True)
+    h.close()
+    ctx.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gd(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -102,7 +102,7 @@ typedef struct gd_options {
     int32_t block_threads;    /* threads per CTA of the edge kernels (default 256) */
     int32_t ctas_per_sm;      /* persistent CTAs per SM (default: occupancy)       */
     int32_t smem_table_max;   /* wedge-table entries kept in shared memory per CTA
-                                 before the global table is used (default 12288) */
+                                 before the global table is used (default 8192)  */
     int32_t reserved[8];
 } gd_options;
 
@@ -165,6 +165,36 @@ int gd_count_per_edge(gd_graph *g, uint64_t *out, int out_flags, gd_u128 global_
 int gd_count_batch(gd_ctx *ctx, int32_t num_graphs, const int32_t *graph_node_ptr,
                    const int32_t *row_ptr, const int32_t *col_idx, int flags,
                    uint64_t *out);
+
+/* ------------------------------------------------------------------------
+ * Measurement and memory hooks (no counterpart in the paper).
+ * ------------------------------------------------------------------------ */
+
+/* Per-kernel device time collected between gd_profile_begin and
+ * gd_profile_end: CUDA events recorded on each graph's stream around every
+ * kernel launch of this context.  name: kernel name; ms_total: summed device
+ * time; launches: number of launches. */
+typedef struct gd_stage_stat {
+    char name[40];
+    double ms_total;
+    int64_t launches;
+} gd_stage_stat;
+
+/* Start collecting (discards what was collected before). */
+int gd_profile_begin(gd_ctx *ctx);
+
+/* Stop, wait for the recorded events, and aggregate per kernel name into
+ * out[0 .. min(*num_out, max_out)).  *num_out receives the number of distinct
+ * kernels.  out may be NULL to query the count. */
+int gd_profile_end(gd_ctx *ctx, gd_stage_stat *out, int32_t max_out, int32_t *num_out);
+
+/* Number of kernels this context has launched since gd_init. */
+int64_t gd_kernel_launches(const gd_ctx *ctx);
+
+/* Device blocks of destroyed graphs stay cached in the context for reuse by
+ * later graphs of the same shape (they count against the budget; a budget
+ * refusal first releases them).  This call returns them to CUDA now. */
+int gd_pool_release(gd_ctx *ctx);
 
 #ifdef __cplusplus
 }

@@ -40,22 +40,60 @@ int cuda_fail(gd_ctx *ctx, cudaError_t e, const char *where) {
         if (e_ != cudaSuccess) return cuda_fail((ctx), e_, #call);    \
     } while (0)
 
-// Device allocation accounted against the context budget.
-int dalloc(gd_graph *g, void **p, size_t bytes) {
-    gd_ctx *ctx = g->ctx;
-    if (bytes == 0) bytes = 16;
+size_t round_block(size_t bytes) { return (bytes + 255) & ~(size_t)255; }
+
+// Release every cached block of the context's pool.
+void trim_pool(gd_ctx *ctx) {
+    for (auto &kv : ctx->pool) cudaFree(kv.second);
+    ctx->in_use -= std::min(ctx->in_use, ctx->pooled);
+    ctx->pool.clear();
+    ctx->pooled = 0;
+}
+
+// Device allocation accounted against the context budget.  Blocks released
+// by destroyed graphs are cached in the context and reused for the same
+// rounded size (a later graph of the same shape allocates nothing).
+int ctx_alloc(gd_ctx *ctx, void **p, size_t bytes) {
+    bytes = round_block(bytes ? bytes : 16);
+    auto it = ctx->pool.find(bytes);
+    if (it != ctx->pool.end()) {
+        *p = it->second;
+        ctx->pool.erase(it);
+        ctx->pooled -= bytes;        // stays in in_use: moves from cached to live
+        return GD_OK;
+    }
+    if (ctx->budget && ctx->in_use + bytes > ctx->budget) trim_pool(ctx);
     if (ctx->budget && ctx->in_use + bytes > ctx->budget)
         return fail(ctx, GD_ENOMEM, "device budget exceeded: need %zu more bytes, %zu of %zu in use",
                     bytes, ctx->in_use, ctx->budget);
     cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess && !ctx->pool.empty()) {
+        cudaGetLastError();
+        trim_pool(ctx);
+        e = cudaMalloc(p, bytes);
+    }
     if (e != cudaSuccess) {
         cudaGetLastError();
         *p = nullptr;
         return fail(ctx, GD_ENOMEM, "cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
     }
     ctx->in_use += bytes;
-    g->ws.bytes += bytes;
     return GD_OK;
+}
+
+void ctx_release(gd_ctx *ctx, void *p, size_t bytes) {
+    if (!p) return;
+    ctx->pool.emplace(round_block(bytes ? bytes : 16), p);
+    ctx->pooled += round_block(bytes ? bytes : 16);
+}
+
+int dalloc(gd_graph *g, void **p, size_t bytes) {
+    int rc = ctx_alloc(g->ctx, p, bytes);
+    if (rc == GD_OK) {
+        g->ws.bytes += round_block(bytes ? bytes : 16);
+        g->ws.blocks.emplace_back(*p, round_block(bytes ? bytes : 16));
+    }
+    return rc;
 }
 
 template <typename T>
@@ -65,13 +103,21 @@ int dalloc_n(gd_graph *g, T **p, int64_t count) {
 
 void free_workspace(gd_graph *g) {
     Workspace &w = g->ws;
-    void *ptrs[] = {w.first_up, w.eoff, w.eu, w.ev, w.eslot, w.mate, w.tslot, w.tnode, w.s1, w.au, w.av,
-                    w.dt, w.cacc, w.yacc, w.vlist, w.counters, w.tribuf, w.wtab, w.sums, w.result,
-                    w.status, w.scan_tmp, w.out_buf};
-    for (void *p : ptrs)
-        if (p) cudaFree(p);
-    if (g->ctx) g->ctx->in_use -= std::min(g->ctx->in_use, w.bytes);
+    if (g->ctx)
+        for (auto &b : w.blocks) ctx_release(g->ctx, b.first, b.second);
     w = Workspace();
+}
+
+// Give one block of this graph back to the context pool.
+void release_block(gd_graph *g, void *p) {
+    auto &bl = g->ws.blocks;
+    for (size_t i = 0; i < bl.size(); i++)
+        if (bl[i].first == p) {
+            ctx_release(g->ctx, p, bl[i].second);
+            g->ws.bytes -= bl[i].second;
+            bl.erase(bl.begin() + i);
+            return;
+        }
 }
 
 int32_t tricap_for(gd_graph *g, int variant) {
@@ -114,7 +160,7 @@ int ensure_workspace(gd_graph *g, bool per_edge, int variant) {
     const int32_t warps = tribuf_warps(sms);
     const int64_t need_tri = (int64_t)warps * tricap_for(g, variant) * 3;
     if (w.tribuf_words < need_tri) {
-        if (w.tribuf) { cudaFree(w.tribuf); g->ctx->in_use -= (size_t)w.tribuf_words * 4; w.bytes -= (size_t)w.tribuf_words * 4; w.tribuf = nullptr; }
+        if (w.tribuf) { release_block(g, w.tribuf); w.tribuf = nullptr; }
         if ((rc = dalloc_n(g, &w.tribuf, need_tri))) return rc;
         w.tribuf_words = need_tri;
     }
@@ -160,7 +206,38 @@ int read_results(gd_graph *g, gd_u128 *out) {
     return GD_OK;
 }
 
+cudaEvent_t take_event(gd_ctx *c) {
+    if (!c->evpool.empty()) {
+        cudaEvent_t e = c->evpool.back();
+        c->evpool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
 }  // namespace
+
+namespace gdi {
+
+void prof_begin(gd_ctx *c, cudaStream_t st, const char *name) {
+    c->launches++;
+    if (!c->prof) return;
+    ProfRec r;
+    r.name = name;
+    r.a = take_event(c);
+    r.b = take_event(c);
+    cudaEventRecord(r.a, st);
+    c->recs.push_back(r);
+}
+
+void prof_end(gd_ctx *c, cudaStream_t st) {
+    if (!c->prof || c->recs.empty()) return;
+    cudaEventRecord(c->recs.back().b, st);
+}
+
+}  // namespace gdi
 
 extern "C" {
 
@@ -209,6 +286,9 @@ void gd_destroy(gd_ctx *ctx) {
     std::vector<gd_graph *> gs = ctx->graphs;
     for (gd_graph *g : gs) gd_destroy_graph(g);
     if (ctx->batch_buf) cudaFree(ctx->batch_buf);
+    trim_pool(ctx);
+    for (auto &r : ctx->recs) { ctx->evpool.push_back(r.a); ctx->evpool.push_back(r.b); }
+    for (cudaEvent_t ev : ctx->evpool) cudaEventDestroy(ev);
     if (ctx->stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
 }
@@ -250,22 +330,18 @@ int gd_create_csr(gd_ctx *ctx, int32_t n, int64_t nnz, const int32_t *row_ptr, c
         g->borrowed = true;
     } else {
         size_t bytes = sizeof(int32_t) * ((size_t)n + 1 + (size_t)nnz);
-        if (ctx->budget && ctx->in_use + bytes > ctx->budget) {
-            gd_destroy_graph(g);
-            return fail(ctx, GD_ENOMEM, "device budget exceeded by the CSR (%zu bytes)", bytes);
-        }
-        cudaError_t e = cudaMalloc((void **)&g->rp, bytes);
-        if (e != cudaSuccess) {
-            cudaGetLastError();
+        int arc = ctx_alloc(ctx, (void **)&g->rp, bytes);
+        if (arc) {
+            std::string msg = ctx->err;
             g->rp = nullptr;
             gd_destroy_graph(g);
-            return fail(ctx, GD_ENOMEM, "cudaMalloc of the CSR failed");
+            ctx->err = msg;
+            return arc;
         }
         g->csr_bytes = bytes;
-        ctx->in_use += bytes;
         g->ci = g->rp + (n + 1);
         cudaMemcpyKind kind = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-        e = cudaMemcpyAsync(g->rp, row_ptr, sizeof(int32_t) * ((size_t)n + 1), kind, g->stream);
+        cudaError_t e = cudaMemcpyAsync(g->rp, row_ptr, sizeof(int32_t) * ((size_t)n + 1), kind, g->stream);
         if (e == cudaSuccess && nnz > 0)
             e = cudaMemcpyAsync(g->ci, col_idx, sizeof(int32_t) * (size_t)nnz, kind, g->stream);
         if (e != cudaSuccess) {
@@ -324,10 +400,7 @@ void gd_destroy_graph(gd_graph *g) {
     if (ctx) cudaSetDevice(ctx->device);
     if (g->stream) cudaStreamSynchronize(g->stream);
     free_workspace(g);
-    if (!g->borrowed && g->rp) {
-        cudaFree(g->rp);
-        if (ctx) ctx->in_use -= std::min(ctx->in_use, g->csr_bytes);
-    }
+    if (!g->borrowed && g->rp && ctx) ctx_release(ctx, g->rp, g->csr_bytes);
     if (ctx) {
         auto &v = ctx->graphs;
         v.erase(std::remove(v.begin(), v.end(), g), v.end());
@@ -363,12 +436,7 @@ int gd_count_per_edge(gd_graph *g, uint64_t *out, int out_flags, gd_u128 global_
     const size_t out_bytes = sizeof(uint64_t) * 15 * (size_t)g->m;
     if (!dev_out) {
         if (!g->ws.out_buf || g->ws.out_buf_bytes < out_bytes) {
-            if (g->ws.out_buf) {
-                cudaFree(g->ws.out_buf);
-                ctx->in_use -= g->ws.out_buf_bytes;
-                g->ws.bytes -= g->ws.out_buf_bytes;
-                g->ws.out_buf = nullptr;
-            }
+            if (g->ws.out_buf) { release_block(g, g->ws.out_buf); g->ws.out_buf = nullptr; }
             if ((rc = dalloc(g, (void **)&g->ws.out_buf, out_bytes))) return rc;
             g->ws.out_buf_bytes = out_bytes;
         }
@@ -389,6 +457,52 @@ int gd_count_batch(gd_ctx *ctx, int32_t num_graphs, const int32_t *graph_node_pt
     if (!ctx) return GD_EINVAL;
     (void)num_graphs; (void)graph_node_ptr; (void)row_ptr; (void)col_idx; (void)flags; (void)out;
     return fail(ctx, GD_ENOTIMPL, "gd_count_batch: not built yet");
+}
+
+int gd_profile_begin(gd_ctx *ctx) {
+    if (!ctx) return GD_EINVAL;
+    for (auto &r : ctx->recs) { ctx->evpool.push_back(r.a); ctx->evpool.push_back(r.b); }
+    ctx->recs.clear();
+    ctx->prof = true;
+    return GD_OK;
+}
+
+int gd_profile_end(gd_ctx *ctx, gd_stage_stat *out, int32_t max_out, int32_t *num_out) {
+    if (!ctx) return GD_EINVAL;
+    ctx->prof = false;
+    std::vector<gd_stage_stat> agg;
+    int rc = GD_OK;
+    for (auto &r : ctx->recs) {
+        float ms = 0.f;
+        cudaError_t e = cudaEventSynchronize(r.b);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, r.a, r.b);
+        if (e != cudaSuccess) { rc = cuda_fail(ctx, e, "profile event"); break; }
+        size_t i = 0;
+        while (i < agg.size() && strncmp(agg[i].name, r.name, sizeof(agg[i].name)) != 0) i++;
+        if (i == agg.size()) {
+            gd_stage_stat st;
+            memset(&st, 0, sizeof(st));
+            snprintf(st.name, sizeof(st.name), "%s", r.name);
+            agg.push_back(st);
+        }
+        agg[i].ms_total += ms;
+        agg[i].launches += 1;
+    }
+    for (auto &r : ctx->recs) { ctx->evpool.push_back(r.a); ctx->evpool.push_back(r.b); }
+    ctx->recs.clear();
+    if (num_out) *num_out = (int32_t)agg.size();
+    if (out)
+        for (size_t i = 0; i < agg.size() && (int32_t)i < max_out; i++) out[i] = agg[i];
+    return rc;
+}
+
+int64_t gd_kernel_launches(const gd_ctx *ctx) { return ctx ? ctx->launches : -1; }
+
+int gd_pool_release(gd_ctx *ctx) {
+    if (!ctx) return GD_EINVAL;
+    cudaSetDevice(ctx->device);
+    trim_pool(ctx);
+    return GD_OK;
 }
 
 }  // extern "C"

@@ -141,17 +141,18 @@ __global__ void k_scan_add(int64_t *out, int64_t len, const int64_t *tile_offs) 
 
 // exclusive scan of len values; out[len] receives the total.  tmp needs
 // >= 2 * ceil(len / SCAN_TILE) + 64 entries per level.
-cudaError_t exclusive_scan(const int64_t *in, int64_t *out, int64_t len, int64_t *tmp, cudaStream_t st) {
+cudaError_t exclusive_scan(gd_graph *g, const int64_t *in, int64_t *out, int64_t len, int64_t *tmp) {
+    cudaStream_t st = g->stream;
     int64_t tiles = (len + SCAN_TILE - 1) / SCAN_TILE;
     if (tiles == 0) {
         return cudaMemsetAsync(out, 0, sizeof(int64_t), st);
     }
     int64_t *sums = tmp, *offs = tmp + tiles;
-    k_scan_tiles<<<(unsigned)tiles, SCAN_T, 0, st>>>(in, out, len, sums);
+    GD_LAUNCH(g, "k_scan_tiles", k_scan_tiles, (unsigned)tiles, SCAN_T, 0, in, out, len, sums);
     if (tiles > 1) {
-        cudaError_t e = exclusive_scan(sums, offs, tiles, tmp + 2 * tiles + 1, st);
+        cudaError_t e = exclusive_scan(g, sums, offs, tiles, tmp + 2 * tiles + 1);
         if (e != cudaSuccess) return e;
-        k_scan_add<<<(unsigned)tiles, SCAN_T, 0, st>>>(out, len, offs);
+        GD_LAUNCH(g, "k_scan_add", k_scan_add, (unsigned)tiles, SCAN_T, 0, out, len, offs);
         // total = offs[tiles]
         return cudaMemcpyAsync(out + len, offs + tiles, sizeof(int64_t), cudaMemcpyDeviceToDevice, st);
     }
@@ -741,7 +742,7 @@ cudaError_t max_degree(gd_graph *g, int32_t *out_host) {
     cudaStream_t st = g->stream;
     cudaError_t e = cudaMemsetAsync(w.status + 3, 0, sizeof(int32_t), st);
     if (e) return e;
-    if (g->n > 0) k_max_degree<<<grid_for(g->n, 256, sm_count(g) * 8), 256, 0, st>>>(g->n, g->rp, w.status + 3);
+    if (g->n > 0) GD_LAUNCH(g, "k_max_degree", k_max_degree, grid_for(g->n, 256, sm_count(g) * 8), 256, 0, g->n, g->rp, w.status + 3);
     e = cudaMemcpyAsync(out_host, w.status + 3, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
     if (e) return e;
     e = cudaStreamSynchronize(st);
@@ -755,7 +756,7 @@ cudaError_t validate_csr(gd_graph *g, int32_t *bad_index, int32_t *bad_code) {
     int32_t init[4] = {0, 0x7fffffff, 0, 0};
     cudaError_t e = cudaMemcpyAsync(w.status, init, sizeof(init), cudaMemcpyHostToDevice, st);
     if (e) return e;
-    if (g->n > 0) k_validate<<<grid_for(g->n, 256, sm_count(g) * 8), 256, 0, st>>>(g->n, g->nnz, g->rp, g->ci, w.status);
+    if (g->n > 0) GD_LAUNCH(g, "k_validate", k_validate, grid_for(g->n, 256, sm_count(g) * 8), 256, 0, g->n, g->nnz, g->rp, g->ci, w.status);
     int32_t h[4];
     e = cudaMemcpyAsync(h, w.status, sizeof(h), cudaMemcpyDeviceToHost, st);
     if (e) return e;
@@ -779,21 +780,21 @@ cudaError_t prepare_edges(gd_graph *g) {
     int64_t *cnt = w.scan_tmp;
     int64_t *offs = w.scan_tmp + (n + 1);
     int64_t *tmp = w.scan_tmp + 2 * (int64_t)(n + 1);
-    k_upper_count<<<grid_for(n, 256, sms * 8), 256, 0, st>>>(n, g->rp, g->ci, w.first_up, cnt);
-    e = exclusive_scan(cnt, offs, n, tmp, st);
+    GD_LAUNCH(g, "k_upper_count", k_upper_count, grid_for(n, 256, sms * 8), 256, 0, n, g->rp, g->ci, w.first_up, cnt);
+    e = exclusive_scan(g, cnt, offs, n, tmp);
     if (e) return e;
-    k_narrow<<<grid_for(n + 1, 256, sms * 8), 256, 0, st>>>(offs, w.eoff, n + 1);
-    k_edge_list<<<grid_for((int64_t)n * 32, 256, sms * 8), 256, 0, st>>>(n, g->rp, g->ci, w.first_up, w.eoff,
+    GD_LAUNCH(g, "k_narrow", k_narrow, grid_for(n + 1, 256, sms * 8), 256, 0, offs, w.eoff, n + 1);
+    GD_LAUNCH(g, "k_edge_list", k_edge_list, grid_for((int64_t)n * 32, 256, sms * 8), 256, 0, n, g->rp, g->ci, w.first_up, w.eoff,
                                                                          w.eu, w.ev, w.eslot);
     if (g->m > 0) {
-        k_mate<<<grid_for(g->m, 256, sms * 8), 256, 0, st>>>(g->m, g->rp, g->ci, w.eu, w.ev, w.eslot, w.mate);
-        k_triangles<<<grid_for(g->m * 32, 256, sms * 16), 256, 0, st>>>(g->m, g->rp, g->ci, w.eu, w.ev, w.eslot,
+        GD_LAUNCH(g, "k_mate", k_mate, grid_for(g->m, 256, sms * 8), 256, 0, g->m, g->rp, g->ci, w.eu, w.ev, w.eslot, w.mate);
+        GD_LAUNCH(g, "k_triangles", k_triangles, grid_for(g->m * 32, 256, sms * 16), 256, 0, g->m, g->rp, g->ci, w.eu, w.ev, w.eslot,
                                                                         w.mate, w.tslot);
     }
     e = cudaMemsetAsync(w.counters, 0, 8 * sizeof(int32_t), st);
     if (e) return e;
     const int32_t cap = g->ctx->opt.smem_table_max;
-    k_wedge_estimate<<<grid_for((int64_t)n * 32, 256, sms * 16), 256, 0, st>>>(n, g->rp, g->ci, cap / 2,
+    GD_LAUNCH(g, "k_wedge_estimate", k_wedge_estimate, grid_for((int64_t)n * 32, 256, sms * 16), 256, 0, n, g->rp, g->ci, cap / 2,
                                                                               w.vlist, w.counters);
     return cudaGetLastError();
 }
@@ -803,9 +804,9 @@ cudaError_t run_per_edge_sums(gd_graph *g) {
     cudaStream_t st = g->stream;
     const int sms = sm_count(g);
     if (g->n > 0)
-        k_node<<<grid_for((int64_t)g->n * 32, 256, sms * 16), 256, 0, st>>>(g->n, g->rp, g->ci, w.tslot, w.tnode, w.s1);
+        GD_LAUNCH(g, "k_node", k_node, grid_for((int64_t)g->n * 32, 256, sms * 16), 256, 0, g->n, g->rp, g->ci, w.tslot, w.tnode, w.s1);
     if (g->m > 0)
-        k_tri_sums<<<grid_for(g->m * 32, 256, sms * 16), 256, 0, st>>>(g->m, g->rp, g->ci, w.eu, w.ev, w.tslot,
+        GD_LAUNCH(g, "k_tri_sums", k_tri_sums, grid_for(g->m * 32, 256, sms * 16), 256, 0, g->m, g->rp, g->ci, w.eu, w.ev, w.tslot,
                                                                        w.au, w.av, w.dt);
     return cudaGetLastError();
 }
@@ -829,20 +830,20 @@ cudaError_t run_cliques_cycles(gd_graph *g, int variant) {
     const int32_t tricap = (int32_t)(w.tribuf_words / ((int64_t)warps * 3));
     const unsigned tri_blocks = (unsigned)(warps / (TRI_THREADS / 32));
     if (variant == GD_VARIANT_LITERAL) {
-        k_literal<<<tri_blocks, TRI_THREADS, 0, st>>>(g->m, g->rp, g->ci, w.eu, w.ev, w.eslot, w.tribuf, tricap,
+        GD_LAUNCH(g, "k_literal", k_literal, tri_blocks, TRI_THREADS, 0, g->m, g->rp, g->ci, w.eu, w.ev, w.eslot, w.tribuf, tricap,
                                                       (unsigned long long *)w.cacc, (unsigned long long *)w.yacc,
                                                       w.status);
         return cudaGetLastError();
     }
-    k_cliques_oriented<<<tri_blocks, TRI_THREADS, 0, st>>>(g->m, g->rp, g->ci, w.eu, w.ev, w.eslot, w.mate,
+    GD_LAUNCH(g, "k_cliques_oriented", k_cliques_oriented, tri_blocks, TRI_THREADS, 0, g->m, g->rp, g->ci, w.eu, w.ev, w.eslot, w.mate,
                                                            w.tribuf, tricap, (unsigned long long *)w.cacc, w.status);
     const int32_t cap = g->ctx->opt.smem_table_max;
     const size_t smem = cycle_smem_bytes(cap);
     e = cudaFuncSetAttribute(k_cycles_oriented<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e) return e;
-    k_cycles_oriented<false><<<(unsigned)(sms * 2), 256, smem, st>>>(
+    GD_LAUNCH(g, "k_cycles_smem", k_cycles_oriented<false>, (unsigned)(sms * 2), 256, smem, 
         g->n, g->rp, g->ci, w.vlist, w.counters, (uint32_t)(cap - 1), nullptr, (unsigned long long *)w.yacc);
-    k_cycles_oriented<true><<<(unsigned)w.wtab_ctas, 256, 0, st>>>(
+    GD_LAUNCH(g, "k_cycles_global", k_cycles_oriented<true>, (unsigned)w.wtab_ctas, 256, 0, 
         g->n, g->rp, g->ci, w.vlist, w.counters, 0, w.wtab, (unsigned long long *)w.yacc);
     return cudaGetLastError();
 }
@@ -861,14 +862,14 @@ cudaError_t run_final(gd_graph *g, int variant, bool per_edge, uint64_t *out_dev
     a.tnode = w.tnode; a.s1 = w.s1; a.au = w.au; a.av = w.av; a.dt = w.dt;
     a.cacc = (const unsigned long long *)w.cacc; a.yacc = (const unsigned long long *)w.yacc;
     a.out = out_dev; a.sums = w.sums; a.status = w.status;
-    k_final<<<grid_for(g->m, 256, sms * 8), 256, 0, st>>>(a);
+    GD_LAUNCH(g, "k_final", k_final, grid_for(g->m, 256, sms * 8), 256, 0, a);
     return cudaGetLastError();
 }
 
 // derive_cyc: sum cyc_e is derived from the 4-cycle credits (oriented
 // variant without per-edge restricted counts).
 cudaError_t run_complete(gd_graph *g, int derive_cyc) {
-    k_complete<<<1, 32, 0, g->stream>>>(g->ws.sums, g->n, derive_cyc, g->ws.result, g->ws.status);
+    GD_LAUNCH(g, "k_complete", k_complete, 1, 32, 0, g->ws.sums, g->n, derive_cyc, g->ws.result, g->ws.status);
     return cudaGetLastError();
 }
 

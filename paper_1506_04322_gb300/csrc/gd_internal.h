@@ -6,6 +6,7 @@
 #include <stdint.h>
 #include <stddef.h>
 
+#include <map>
 #include <string>
 #include <vector>
 
@@ -75,9 +76,19 @@ struct Workspace {
     uint64_t *out_buf = nullptr;
     size_t out_buf_bytes = 0;
     size_t bytes = 0;
+    std::vector<std::pair<void *, size_t>> blocks;   // every block above, for release
 };
 
 }  // namespace gdi
+
+
+namespace gdi {
+struct ProfRec {
+    const char *name;
+    cudaEvent_t a, b;
+};
+}  // namespace gdi
+
 
 struct gd_ctx {
     int device = 0;
@@ -91,6 +102,14 @@ struct gd_ctx {
     // batch scratch (grown on demand)
     void *batch_buf = nullptr;
     size_t batch_bytes = 0;
+    // caching allocator: released device blocks by size, reused by later graphs
+    std::multimap<size_t, void *> pool;
+    size_t pooled = 0;
+    // stage timing (CUDA events around each launch while enabled)
+    bool prof = false;
+    std::vector<gdi::ProfRec> recs;
+    std::vector<cudaEvent_t> evpool;
+    int64_t launches = 0;
 };
 
 struct gd_graph {
@@ -109,6 +128,11 @@ struct gd_graph {
 
 namespace gdi {
 
+// launch bookkeeping (gd_api.cu): launch counter and, while profiling, an
+// event pair around the launch on the graph's stream
+void prof_begin(gd_ctx *c, cudaStream_t st, const char *name);
+void prof_end(gd_ctx *c, cudaStream_t st);
+
 // kernels (gd_count.cu)
 cudaError_t validate_csr(gd_graph *g, int32_t *bad_index_host, int32_t *bad_code_host);
 cudaError_t prepare_edges(gd_graph *g);                   // edge list, mate, T per slot
@@ -124,3 +148,10 @@ int batch_count(gd_ctx *ctx, int32_t num_graphs, const int32_t *gnp, const int32
                 const int32_t *ci, int64_t nnz, int32_t ntot, uint64_t *out_dev);
 
 }  // namespace gdi
+
+#define GD_LAUNCH(G, NAME, KERNEL, GRID, BLOCK, SMEM, ...)                      \
+    do {                                                                        \
+        gdi::prof_begin((G)->ctx, (G)->stream, NAME);                           \
+        KERNEL<<<(GRID), (BLOCK), (SMEM), (G)->stream>>>(__VA_ARGS__);          \
+        gdi::prof_end((G)->ctx, (G)->stream);                                   \
+    } while (0)

@@ -47,6 +47,10 @@ class gd_u128(ctypes.Structure):
     _fields_ = [("lo", ctypes.c_uint64), ("hi", ctypes.c_uint64)]
 
 
+class gd_stage_stat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 40), ("ms_total", ctypes.c_double), ("launches", ctypes.c_int64)]
+
+
 class gd_options(ctypes.Structure):
     _fields_ = [("variant", ctypes.c_int32), ("block_threads", ctypes.c_int32),
                 ("ctas_per_sm", ctypes.c_int32), ("smem_table_max", ctypes.c_int32),
@@ -80,6 +84,10 @@ def load():
             "gd_count_global": (ctypes.c_int, [vp, vp]),
             "gd_count_per_edge": (ctypes.c_int, [vp, vp, ctypes.c_int, vp]),
             "gd_count_batch": (ctypes.c_int, [vp, i32, vp, vp, vp, ctypes.c_int, vp]),
+            "gd_profile_begin": (ctypes.c_int, [vp]),
+            "gd_profile_end": (ctypes.c_int, [vp, vp, i32, ctypes.POINTER(i32)]),
+            "gd_kernel_launches": (i64, [vp]),
+            "gd_pool_release": (ctypes.c_int, [vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -175,6 +183,26 @@ def gd_count_batch(ctx, num_graphs: int, graph_node_ptr: int, row_ptr: int, col_
            "gd_count_batch")
 
 
+def gd_profile_begin(ctx) -> None:
+    _check(ctx, load().gd_profile_begin(ctx), "gd_profile_begin")
+
+
+def gd_profile_end(ctx) -> dict:
+    """{kernel name: (total ms, launches)} collected since gd_profile_begin."""
+    num = ctypes.c_int32()
+    buf = (gd_stage_stat * 64)()
+    _check(ctx, load().gd_profile_end(ctx, buf, 64, ctypes.byref(num)), "gd_profile_end")
+    return {buf[i].name.decode(): (buf[i].ms_total, buf[i].launches) for i in range(min(num.value, 64))}
+
+
+def gd_kernel_launches(ctx) -> int:
+    return int(load().gd_kernel_launches(ctx))
+
+
+def gd_pool_release(ctx) -> None:
+    _check(ctx, load().gd_pool_release(ctx), "gd_pool_release")
+
+
 # ---------------------------------------------------------------------------
 # object layer
 # ---------------------------------------------------------------------------
@@ -234,6 +262,15 @@ class Context:
     @property
     def last_error(self) -> str:
         return gd_last_error(self.handle)
+
+    def profile_begin(self) -> None:
+        gd_profile_begin(self.handle)
+
+    def profile_end(self) -> dict:
+        return gd_profile_end(self.handle)
+
+    def kernel_launches(self) -> int:
+        return gd_kernel_launches(self.handle)
 
     def graph(self, row_ptr, col_idx=None, n: int | None = None, validate: bool = False,
               borrow: bool = False, stream: int | None = None) -> "Graph":
