@@ -196,6 +196,37 @@ int64_t gd_kernel_launches(const gd_ctx *ctx);
  * refusal first releases them).  This call returns them to CUDA now. */
 int gd_pool_release(gd_ctx *ctx);
 
+/* ------------------------------------------------------------------------
+ * Counting without allocating (no counterpart in the paper).
+ *
+ * For callers that must not allocate device memory: code running next to a
+ * latency-critical pipeline (cudaMalloc/cudaFree may synchronize the device
+ * and stall the other streams), plug-ins whose host framework owns every
+ * device byte through its own allocator, and processes under a fixed device
+ * memory quota.  The scratch is one static array inside libgd's device image
+ * (GD_STATIC_SCRATCH_BYTES on every GPU that loads the library, held until
+ * the process exits); nothing is allocated per call.
+ * ------------------------------------------------------------------------ */
+#define GD_STATIC_MAX_N 32768              /* largest n accepted            */
+#define GD_STATIC_MAX_NNZ 262144           /* largest nnz (= 2|E|) accepted */
+#define GD_STATIC_SCRATCH_BYTES 5505024    /* 5.25 MiB of static scratch    */
+
+/* The 15 global counts of gd_count_global (same order, exact), for a graph
+ * with n <= GD_STATIC_MAX_N and nnz <= GD_STATIC_MAX_NNZ.  row_ptr, col_idx
+ * and out (15 gd_u128) are DEVICE pointers owned by the caller; the kernel
+ * runs on cuda_stream (NULL: legacy default stream) on the current device and
+ * the call waits for it.  Returns GD_EOVERFLOW for larger graphs (nothing is
+ * launched), GD_EINVAL for a malformed CSR (same checks as gd_create_csr),
+ * GD_ECUDA on a CUDA error.
+ * The first call on each device looks up the scratch address
+ * (cudaGetSymbolAddress) with that device current: make it before any stream
+ * capture on that device.  All calls on a device share the one scratch
+ * array, which keeps the last call's contents (each call clears what must
+ * start at zero): calls whose kernels overlap on the GPU race and must be
+ * serialized by the caller. */
+int gd_count_global_static(int32_t n, int64_t nnz, const int32_t *row_ptr, const int32_t *col_idx,
+                           gd_u128 *out, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -88,6 +88,7 @@ def load():
             "gd_profile_end": (ctypes.c_int, [vp, vp, i32, ctypes.POINTER(i32)]),
             "gd_kernel_launches": (i64, [vp]),
             "gd_pool_release": (ctypes.c_int, [vp]),
+            "gd_count_global_static": (ctypes.c_int, [i32, i64, vp, vp, vp, vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -201,6 +202,16 @@ def gd_kernel_launches(ctx) -> int:
 
 def gd_pool_release(ctx) -> None:
     _check(ctx, load().gd_pool_release(ctx), "gd_pool_release")
+
+
+GD_STATIC_MAX_N = 32768
+GD_STATIC_MAX_NNZ = 262144
+
+
+def gd_count_global_static(n: int, nnz: int, row_ptr: int, col_idx: int, out: int, stream: int = 0) -> int:
+    """Global counts without allocating (device pointers in and out; see
+    include/gd.h).  Returns the gd_status code."""
+    return int(load().gd_count_global_static(n, nnz, row_ptr, col_idx, out, stream or None))
 
 
 # ---------------------------------------------------------------------------
