@@ -52,6 +52,10 @@ def parse():
     ap.add_argument("--impl", default="gd", choices=["gd", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--smem-table", type=int, default=None, help="gd_options.smem_table_max")
+    ap.add_argument("--bitmap-max", type=int, default=None, help="gd_options.bitmap_max_outdeg")
+    ap.add_argument("--hub-log2", type=int, default=None, help="gd_options.hub_wedges_log2")
+    ap.add_argument("--global-only", action="store_true", help="time gd_count_global instead")
     return ap.parse_args()
 
 
@@ -228,7 +232,8 @@ def run_gd(args):
     g = inputs.chung_lu_1m()
     m = g.m
 
-    ctx = gd.Context(device)
+    ctx = gd.Context(device, smem_table_max=args.smem_table, bitmap_max_outdeg=args.bitmap_max,
+                     hub_wedges_log2=args.hub_log2)
     stream = torch.cuda.Stream(device=device)
     rp = torch.from_numpy(g.row_ptr).to(device)
     ci = torch.from_numpy(g.col_idx).to(device)
@@ -238,6 +243,8 @@ def run_gd(args):
     h = ctx.graph(rp, ci, n=g.n, borrow=True, stream=stream.cuda_stream)
 
     def step():
+        if args.global_only:
+            return h.count_global()
         return h.count_per_edge(out=out)[1]
 
     for _ in range(max(3, args.warmup)):
@@ -345,7 +352,8 @@ def run_gd(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-        "config": {"workload": g.name, "n": g.n, "m": g.m, "mode": "per-edge (15 columns) + global",
+        "config": {"workload": g.name, "n": g.n, "m": g.m,
+                   "mode": "global" if args.global_only else "per-edge (15 columns) + global",
                    "variant": "oriented", "seed": 2, "l2": "flushed between timed steps (512 MB write)",
                    "parallelism": f"replicas x{ws}"},
         "e2e": {"value": ws * m / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},

@@ -102,8 +102,16 @@ typedef struct gd_options {
     int32_t block_threads;    /* threads per CTA of the edge kernels (default 256) */
     int32_t ctas_per_sm;      /* persistent CTAs per SM (default: occupancy)       */
     int32_t smem_table_max;   /* wedge-table entries kept in shared memory per CTA
-                                 before the global table is used (default 8192)  */
-    int32_t reserved[8];
+                                 (power of two in [256, 16384], default 8192);
+                                 vertices with at most half as many wedges use it */
+    int32_t bitmap_max_outdeg;   /* nodes with at most this many higher-ranked
+                                    neighbours get the shared-memory adjacency
+                                    (bitmap) triangle/4-clique kernel; a graph
+                                    with a larger out-degree uses pairwise tests
+                                    (default and maximum 1024, minimum 2)       */
+    int32_t hub_wedges_log2;  /* vertices with more than 2^k wedges are processed
+                                 by the whole GPU in batches (default 18)       */
+    int32_t reserved[6];
 } gd_options;
 
 /* Fill *opt with the defaults. */

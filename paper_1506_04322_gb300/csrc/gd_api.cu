@@ -132,10 +132,9 @@ int32_t tricap_for(gd_graph *g, int variant) {
 
 // Allocate everything a count call needs (kept across calls; contents are
 // recomputed by every call).
-int ensure_workspace(gd_graph *g, bool per_edge, int variant) {
+int ensure_workspace(gd_graph *g, bool per_edge) {
     Workspace &w = g->ws;
     const int64_t n = g->n, m = g->m, nnz = g->nnz;
-    const int sms = g->ctx->num_sms;
     int rc;
     if (!w.status) {
         if ((rc = dalloc_n(g, &w.status, 4))) return rc;
@@ -149,24 +148,29 @@ int ensure_workspace(gd_graph *g, bool per_edge, int variant) {
         if ((rc = dalloc_n(g, &w.eslot, m))) return rc;
         if ((rc = dalloc_n(g, &w.mate, nnz))) return rc;
         if ((rc = dalloc_n(g, &w.tslot, nnz))) return rc;
+        if ((rc = dalloc_n(g, &w.tcred, nnz))) return rc;
+        if ((rc = dalloc_n(g, &w.nd, nnz))) return rc;
         if ((rc = dalloc_n(g, &w.vlist, n))) return rc;
-        if ((rc = dalloc_n(g, &w.counters, 8))) return rc;
+        if ((rc = dalloc_n(g, &w.hubs, n))) return rc;
+        if ((rc = dalloc_n(g, &w.clist, 4 * n))) return rc;
+        if ((rc = dalloc_n(g, &w.counters, C_NUM))) return rc;
+        if ((rc = dalloc_n(g, &w.dag_off, n + 1))) return rc;
+        if ((rc = dalloc_n(g, &w.dag_col, m))) return rc;
+        if ((rc = dalloc_n(g, &w.dag_slot, m))) return rc;
+        if ((rc = dalloc_n(g, &w.dag_nd, m))) return rc;
         if ((rc = dalloc_n(g, &w.sums, 2 * (S_NUM + X_NUM)))) return rc;
         if ((rc = dalloc_n(g, &w.result, 30))) return rc;
         if ((rc = dalloc_n(g, &w.scan_tmp, 3 * (n + 1) + 4096))) return rc;
         if ((rc = dalloc_n(g, &w.cacc, nnz))) return rc;
         if ((rc = dalloc_n(g, &w.yacc, nnz))) return rc;
-    }
-    const int32_t warps = tribuf_warps(sms);
-    const int64_t need_tri = (int64_t)warps * tricap_for(g, variant) * 3;
-    if (w.tribuf_words < need_tri) {
-        if (w.tribuf) { release_block(g, w.tribuf); w.tribuf = nullptr; }
-        if ((rc = dalloc_n(g, &w.tribuf, need_tri))) return rc;
-        w.tribuf_words = need_tri;
+        if ((rc = dalloc_n(g, &w.tcount, 64))) return rc;
+        if ((rc = dalloc_n(g, &w.mlist, n))) return rc;
+        if ((rc = dalloc_n(g, &w.west, n))) return rc;
     }
     if (!w.wtab && n > 0) {
-        w.wtab_ctas = sms;
+        w.wtab_ctas = table_slots(g);
         if ((rc = dalloc_n(g, &w.wtab, (int64_t)w.wtab_ctas * n))) return rc;
+        if ((rc = dalloc_n(g, &w.touched, (int64_t)w.wtab_ctas * n))) return rc;
         GD_CK(g->ctx, cudaMemset(w.wtab, 0, sizeof(uint32_t) * (size_t)w.wtab_ctas * n));
     }
     if (per_edge && !w.tnode) {
@@ -176,6 +180,18 @@ int ensure_workspace(gd_graph *g, bool per_edge, int variant) {
         if ((rc = dalloc_n(g, &w.av, m))) return rc;
         if ((rc = dalloc_n(g, &w.dt, m))) return rc;
     }
+    return GD_OK;
+}
+
+// Candidate buffers of the literal and pairwise-clique kernels.
+int ensure_tribuf(gd_graph *g, int variant) {
+    Workspace &w = g->ws;
+    const int64_t need = (int64_t)tribuf_warps(g->ctx->num_sms) * tricap_for(g, variant) * 3;
+    if (w.tribuf_words >= need) return GD_OK;
+    if (w.tribuf) { release_block(g, w.tribuf); w.tribuf = nullptr; w.tribuf_words = 0; }
+    int rc = dalloc_n(g, &w.tribuf, need);
+    if (rc) return rc;
+    w.tribuf_words = need;
     return GD_OK;
 }
 
@@ -248,6 +264,8 @@ void gd_default_options(gd_options *opt) {
     opt->block_threads = 256;
     opt->ctas_per_sm = 0;
     opt->smem_table_max = 8192;
+    opt->bitmap_max_outdeg = gdi::CL_D2;
+    opt->hub_wedges_log2 = 21;
 }
 
 int gd_init(gd_ctx **ctx_out, int device, size_t hbm_budget_bytes, const gd_options *opt) {
@@ -267,6 +285,13 @@ int gd_init(gd_ctx **ctx_out, int device, size_t hbm_budget_bytes, const gd_opti
             return rc;
         }
         if (ctx->opt.variant < 0 || ctx->opt.variant > 2) { delete ctx; return GD_EINVAL; }
+        if (ctx->opt.bitmap_max_outdeg == 0) ctx->opt.bitmap_max_outdeg = gdi::CL_D2;
+        if (ctx->opt.hub_wedges_log2 == 0) ctx->opt.hub_wedges_log2 = 21;
+        if (ctx->opt.bitmap_max_outdeg < 2 || ctx->opt.bitmap_max_outdeg > gdi::CL_D2 ||
+            ctx->opt.hub_wedges_log2 < 4 || ctx->opt.hub_wedges_log2 > 40) {
+            delete ctx;
+            return GD_EINVAL;
+        }
     }
     cudaError_t e = cudaSetDevice(device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
@@ -408,18 +433,49 @@ void gd_destroy_graph(gd_graph *g) {
     delete g;
 }
 
+// The whole single-graph path (rows a1-a8); per_edge writes the 15 columns
+// to out_dev.
+static int count_path(gd_graph *g, bool per_edge, uint64_t *out_dev) {
+    gd_ctx *ctx = g->ctx;
+    const int variant = resolve_variant(g);
+    int rc = ensure_workspace(g, per_edge);
+    if (rc) return rc;
+    GD_CK(ctx, prepare_edges(g));
+    if (variant == GD_VARIANT_LITERAL) {
+        if ((rc = ensure_tribuf(g, variant))) return rc;
+        GD_CK(ctx, run_triangles_intersect(g));
+        if (per_edge) GD_CK(ctx, run_per_edge_sums(g));
+        GD_CK(ctx, run_literal(g));
+        GD_CK(ctx, run_final(g, variant, per_edge, false, out_dev));
+        GD_CK(ctx, run_complete(g, 0));
+        return GD_OK;
+    }
+    int32_t cnt[C_NUM];
+    GD_CK(ctx, run_schedule(g, cnt));
+    bool cliq_credits = per_edge;
+    if (cnt[C_CL0 + 3] > 0) {
+        // an out-degree above the bitmap kernels' limit: pairwise clique tests
+        if ((rc = ensure_tribuf(g, variant))) return rc;
+        GD_CK(ctx, run_triangles_intersect(g));
+        GD_CK(ctx, run_cliques_pairwise(g));
+        cliq_credits = true;
+    } else {
+        GD_CK(ctx, run_triangles_cliques(g, per_edge, cnt));
+    }
+    if (per_edge) GD_CK(ctx, run_per_edge_sums(g));
+    GD_CK(ctx, run_cycles(g, per_edge, cnt));
+    GD_CK(ctx, run_final(g, variant, per_edge, cliq_credits, out_dev));
+    GD_CK(ctx, run_complete(g, per_edge ? 0 : 1));
+    return GD_OK;
+}
+
 int gd_count_global(gd_graph *g, gd_u128 out[15]) {
     if (!g || !out) return GD_EINVAL;
     gd_ctx *ctx = g->ctx;
     ctx->err.clear();
     GD_CK(ctx, cudaSetDevice(ctx->device));
-    const int variant = resolve_variant(g);
-    int rc = ensure_workspace(g, false, variant);
+    int rc = count_path(g, false, nullptr);
     if (rc) return rc;
-    GD_CK(ctx, prepare_edges(g));
-    GD_CK(ctx, run_cliques_cycles(g, variant));
-    GD_CK(ctx, run_final(g, variant, false, nullptr));
-    GD_CK(ctx, run_complete(g, variant == GD_VARIANT_LITERAL ? 0 : 1));
     return read_results(g, out);
 }
 
@@ -428,12 +484,10 @@ int gd_count_per_edge(gd_graph *g, uint64_t *out, int out_flags, gd_u128 global_
     gd_ctx *ctx = g->ctx;
     ctx->err.clear();
     GD_CK(ctx, cudaSetDevice(ctx->device));
-    const int variant = resolve_variant(g);
-    int rc = ensure_workspace(g, true, variant);
-    if (rc) return rc;
     uint64_t *dst = out;
     const bool dev_out = (out_flags & GD_OUT_DEVICE) != 0;
     const size_t out_bytes = sizeof(uint64_t) * 15 * (size_t)g->m;
+    int rc;
     if (!dev_out) {
         if (!g->ws.out_buf || g->ws.out_buf_bytes < out_bytes) {
             if (g->ws.out_buf) { release_block(g, g->ws.out_buf); g->ws.out_buf = nullptr; }
@@ -442,11 +496,8 @@ int gd_count_per_edge(gd_graph *g, uint64_t *out, int out_flags, gd_u128 global_
         }
         dst = g->ws.out_buf;
     }
-    GD_CK(ctx, prepare_edges(g));
-    GD_CK(ctx, run_per_edge_sums(g));
-    GD_CK(ctx, run_cliques_cycles(g, variant));
-    GD_CK(ctx, run_final(g, variant, true, dst));
-    GD_CK(ctx, run_complete(g, 0));
+    rc = count_path(g, true, dst);
+    if (rc) return rc;
     if (!dev_out && g->m > 0)
         GD_CK(ctx, cudaMemcpyAsync(out, dst, out_bytes, cudaMemcpyDeviceToHost, g->stream));
     return read_results(g, global_out);

@@ -21,52 +21,14 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "gd_device.cuh"
 #include "gd_internal.h"
 
 namespace gdi {
 
 namespace {
 
-constexpr int WARP = 32;
-
-__device__ __forceinline__ int32_t ldg(const int32_t *p) { return __ldg(p); }
-
-__device__ __forceinline__ bool precedes(int32_t da, int32_t a, int32_t db, int32_t b) {
-    return da < db || (da == db && a < b);
-}
-
-// first index i in [0,len) with a[i] >= key (len if none)
-__device__ __forceinline__ int32_t lower_bound(const int32_t *a, int32_t len, int32_t key) {
-    int32_t lo = 0;
-    while (len > 0) {
-        int32_t half = len >> 1;
-        if (ldg(a + lo + half) < key) { lo += half + 1; len -= half + 1; }
-        else len = half;
-    }
-    return lo;
-}
-
-__device__ __forceinline__ int32_t find_in(const int32_t *a, int32_t len, int32_t key) {
-    int32_t i = lower_bound(a, len, key);
-    return (i < len && ldg(a + i) == key) ? i : -1;
-}
-
-template <typename T>
-__device__ __forceinline__ T warp_sum(T x) {
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-    return x;
-}
-
-// u128 accumulation into (lo, hi) words
-__device__ __forceinline__ void add_u128(unsigned long long *lohi, unsigned long long x) {
-    if (x == 0) return;
-    unsigned long long old = atomicAdd(lohi, x);
-    if (old + x < old) atomicAdd(lohi + 1, 1ull);
-}
-
-__device__ __forceinline__ int global_warp() { return (blockIdx.x * blockDim.x + threadIdx.x) >> 5; }
-__device__ __forceinline__ int num_warps() { return (gridDim.x * blockDim.x) >> 5; }
-__device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
+using namespace gdi::dev;
 
 // ---------------------------------------------------------------------------
 // CSR validation: sorted rows, ids in range, no self-loops, symmetric.
@@ -338,156 +300,6 @@ __global__ void k_cliques_oriented(int64_t m, const int32_t *__restrict__ rp, co
 }
 
 // ---------------------------------------------------------------------------
-// Step 2, oriented 4-cycles: every 4-cycle once, from its highest-ranked node
-// u with opposite node y; wedge (u, v, y) with v, y ranked below u.  A wedge
-// table counts cnt[y] = number of such v; then each wedge carries cnt[y]-1
-// cycles, credited to edges (u,v) and (v,y).  Slot credits sum, per edge, to
-// the number of (not necessarily induced) 4-cycles through the edge.
-// ---------------------------------------------------------------------------
-
-// est[u] = sum_{v in N(u), v below u} d_v  (upper bound on wedges at u)
-__global__ void k_wedge_estimate(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
-                                 int32_t small_cap, int32_t *vlist, int32_t *counters) {
-    const int lane = lane_id();
-    for (int32_t u = global_warp(); u < n; u += num_warps()) {
-        int32_t bu = rp[u], du = rp[u + 1] - bu;
-        int64_t est = 0;
-        int32_t dplus = 0;
-        for (int32_t i = lane; i < du; i += WARP) {
-            int32_t v = ci[bu + i];
-            int32_t dv = rp[v + 1] - rp[v];
-            if (precedes(dv, v, du, u)) est += dv; else dplus++;
-        }
-        est = warp_sum(est);
-        dplus = warp_sum(dplus);
-        if (lane == 0) {
-            atomicMax(counters + 2, dplus);
-            if (est > 0) {
-                if (est <= small_cap) {
-                    int32_t pos = atomicAdd(counters + 0, 1);
-                    vlist[pos] = u;
-                } else {
-                    int32_t pos = atomicAdd(counters + 1, 1);
-                    vlist[n - 1 - pos] = u;     // big tier fills from the back
-                }
-            }
-        }
-    }
-}
-
-__device__ __forceinline__ uint32_t hash32(uint32_t x) {
-    x ^= x >> 16; x *= 0x7feb352dU; x ^= x >> 15; x *= 0x846ca68bU; x ^= x >> 16;
-    return x;
-}
-
-// shared-memory open-addressing table lookup (keys -1 = empty); the table
-// holds at most cap/2 keys, so every probe sequence ends.
-__device__ __forceinline__ uint32_t smem_get(const int32_t *keys, const uint32_t *vals, uint32_t capmask, int32_t y) {
-    uint32_t h = hash32((uint32_t)y) & capmask;
-    for (uint32_t probes = 0; probes <= capmask; probes++) {
-        int32_t k = keys[h];
-        if (k == y) return vals[h];
-        if (k == -1) return 0;
-        h = (h + 1) & capmask;
-    }
-    return 0;
-}
-
-template <bool GLOBAL_TABLE>
-__global__ void k_cycles_oriented(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
-                                  const int32_t *__restrict__ vlist_base, const int32_t *__restrict__ counters,
-                                  uint32_t capmask, uint32_t *wtab, unsigned long long *yacc) {
-    extern __shared__ int32_t sm[];
-    __shared__ int32_t ntouched;
-    int32_t *keys = sm;
-    uint32_t *vals = (uint32_t *)(sm + (capmask + 1));
-    int32_t *touched = sm + 2 * (capmask + 1);
-    // small tier: vlist_base[0 .. counters[0]); big tier: the last counters[1] entries
-    const int32_t nv = GLOBAL_TABLE ? counters[1] : counters[0];
-    const int32_t *vlist = GLOBAL_TABLE ? vlist_base + (n - nv) : vlist_base;
-    uint32_t *tab = GLOBAL_TABLE ? wtab + (int64_t)blockIdx.x * n : nullptr;
-    const int lane = lane_id(), warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    if (!GLOBAL_TABLE) {
-        for (uint32_t i = threadIdx.x; i <= capmask; i += blockDim.x) { keys[i] = -1; vals[i] = 0; }
-        if (threadIdx.x == 0) ntouched = 0;
-    }
-    __syncthreads();
-    for (int32_t idx = blockIdx.x; idx < nv; idx += gridDim.x) {
-        const int32_t u = vlist[idx];
-        const int32_t bu = rp[u], du = rp[u + 1] - bu;
-        // phase 1: count wedges per y
-        for (int32_t i = warp; i < du; i += nwarps) {
-            int32_t v = ci[bu + i];
-            int32_t bv = rp[v], dv = rp[v + 1] - bv;
-            if (!precedes(dv, v, du, u)) continue;
-            for (int32_t j = lane; j < dv; j += WARP) {
-                int32_t y = ci[bv + j];
-                int32_t dy = rp[y + 1] - rp[y];
-                if (!precedes(dy, y, du, u)) continue;
-                if (GLOBAL_TABLE) {
-                    atomicAdd(tab + y, 1u);
-                } else {
-                    uint32_t h = hash32((uint32_t)y) & capmask;
-                    while (true) {
-                        int32_t k = keys[h];
-                        if (k == y) { atomicAdd(vals + h, 1u); break; }
-                        if (k == -1) {
-                            int32_t old = atomicCAS(keys + h, -1, y);
-                            if (old == -1) {
-                                atomicAdd(vals + h, 1u);
-                                touched[atomicAdd(&ntouched, 1)] = (int32_t)h;
-                                break;
-                            }
-                            if (old == y) { atomicAdd(vals + h, 1u); break; }
-                        }
-                        h = (h + 1) & capmask;
-                    }
-                }
-            }
-        }
-        __syncthreads();
-        // phase 2: credit cnt[y]-1 to (v,y) and (u,v)
-        for (int32_t i = warp; i < du; i += nwarps) {
-            int32_t v = ci[bu + i];
-            int32_t bv = rp[v], dv = rp[v + 1] - bv;
-            if (!precedes(dv, v, du, u)) continue;
-            unsigned long long s = 0;
-            for (int32_t j = lane; j < dv; j += WARP) {
-                int32_t y = ci[bv + j];
-                int32_t dy = rp[y + 1] - rp[y];
-                if (!precedes(dy, y, du, u)) continue;
-                uint32_t c = GLOBAL_TABLE ? tab[y] : smem_get(keys, vals, capmask, y);
-                if (c > 1) {
-                    atomicAdd(yacc + (bv + j), (unsigned long long)(c - 1));
-                    s += c - 1;
-                }
-            }
-            s = warp_sum(s);
-            if (lane == 0 && s) atomicAdd(yacc + (bu + i), s);
-        }
-        __syncthreads();
-        // phase 3: clear what this vertex touched
-        if (GLOBAL_TABLE) {
-            for (int32_t i = warp; i < du; i += nwarps) {
-                int32_t v = ci[bu + i];
-                int32_t bv = rp[v], dv = rp[v + 1] - bv;
-                if (!precedes(dv, v, du, u)) continue;
-                for (int32_t j = lane; j < dv; j += WARP) tab[ci[bv + j]] = 0;
-            }
-        } else {
-            const int32_t nt = ntouched;
-            for (int32_t i = threadIdx.x; i < nt; i += blockDim.x) {
-                int32_t h = touched[i];
-                keys[h] = -1; vals[h] = 0;
-            }
-        }
-        __syncthreads();
-        if (!GLOBAL_TABLE && threadIdx.x == 0) ntouched = 0;
-        __syncthreads();
-    }
-}
-
-// ---------------------------------------------------------------------------
 // Step 2, literal (Algorithm 2 CliqueCount / CycleCount), warp per edge.
 // cliq_e: for w in Tri_e, r in N(w): r in Tri_e (each internal edge seen
 // twice; the paper's X(w)=0 reset halves it the same way).
@@ -564,6 +376,7 @@ struct FinalArgs {
     int variant;              // 1 literal, 2 oriented
     int per_edge;             // write columns
     int need_restricted;      // per-edge restricted counts available
+    int cliq_credits;         // cliq_e from the per-slot credits (else summed by the clique kernel)
     const int32_t *rp, *eu, *ev, *eslot, *mate;
     const uint32_t *tslot;
     const uint64_t *tnode, *s1, *au, *av, *dt;
@@ -600,16 +413,19 @@ __global__ void k_final(FinalArgs a) {
         if (a.variant == GD_VARIANT_LITERAL) {
             cliq = (int64_t)a.cacc[p];
             cyc = (int64_t)a.yacc[p];
-        } else {
+            loc[S_CLIQ] += cliq;
+        } else if (a.cliq_credits) {
             const int32_t q = a.mate[p];
             cliq = (int64_t)(a.cacc[p] + a.cacc[q]);
-            c4 = (int64_t)(a.yacc[p] + a.yacc[q]);
-            loc[X_C4 + S_NUM] += c4;
+            loc[S_CLIQ] += cliq;
         }
-        loc[S_CLIQ] += cliq;
         if (!a.need_restricted) {
             loc[S_CYC] += cyc;
             continue;
+        }
+        if (a.variant != GD_VARIANT_LITERAL) {
+            const int32_t q = a.mate[p];
+            c4 = (int64_t)(a.yacc[p] + a.yacc[q]);
         }
         const int64_t tsu = (int64_t)a.au[k] - T - 2 * cliq;
         const int64_t tsv = (int64_t)a.av[k] - T - 2 * cliq;
@@ -727,6 +543,10 @@ inline unsigned grid_for(int64_t items, int per_block, int max_blocks) {
 // host launchers (all asynchronous on the graph's stream)
 // ===========================================================================
 
+cudaError_t exclusive_scan_i64(gd_graph *g, const int64_t *in, int64_t *out, int64_t len, int64_t *tmp) {
+    return exclusive_scan(g, in, out, len, tmp);
+}
+
 static int sm_count(gd_graph *g) { return g->ctx->num_sms > 0 ? g->ctx->num_sms : 152; }
 
 __global__ void k_max_degree(int32_t n, const int32_t *__restrict__ rp, int32_t *out) {
@@ -776,6 +596,8 @@ cudaError_t prepare_edges(gd_graph *g) {
     const int32_t n = g->n;
     cudaError_t e = cudaMemsetAsync(w.status, 0, 4 * sizeof(int32_t), st);
     if (e) return e;
+    e = cudaMemsetAsync(w.sums, 0, sizeof(unsigned long long) * 2 * (S_NUM + X_NUM), st);
+    if (e) return e;
     if (n == 0) return cudaSuccess;
     int64_t *cnt = w.scan_tmp;
     int64_t *offs = w.scan_tmp + (n + 1);
@@ -786,16 +608,18 @@ cudaError_t prepare_edges(gd_graph *g) {
     GD_LAUNCH(g, "k_narrow", k_narrow, grid_for(n + 1, 256, sms * 8), 256, 0, offs, w.eoff, n + 1);
     GD_LAUNCH(g, "k_edge_list", k_edge_list, grid_for((int64_t)n * 32, 256, sms * 8), 256, 0, n, g->rp, g->ci, w.first_up, w.eoff,
                                                                          w.eu, w.ev, w.eslot);
-    if (g->m > 0) {
+    if (g->m > 0)
         GD_LAUNCH(g, "k_mate", k_mate, grid_for(g->m, 256, sms * 8), 256, 0, g->m, g->rp, g->ci, w.eu, w.ev, w.eslot, w.mate);
-        GD_LAUNCH(g, "k_triangles", k_triangles, grid_for(g->m * 32, 256, sms * 16), 256, 0, g->m, g->rp, g->ci, w.eu, w.ev, w.eslot,
-                                                                        w.mate, w.tslot);
-    }
-    e = cudaMemsetAsync(w.counters, 0, 8 * sizeof(int32_t), st);
-    if (e) return e;
-    const int32_t cap = g->ctx->opt.smem_table_max;
-    GD_LAUNCH(g, "k_wedge_estimate", k_wedge_estimate, grid_for((int64_t)n * 32, 256, sms * 16), 256, 0, n, g->rp, g->ci, cap / 2,
-                                                                              w.vlist, w.counters);
+    return cudaGetLastError();
+}
+
+// Step 1 by per-edge intersection (literal variant and out-degree fallback)
+cudaError_t run_triangles_intersect(gd_graph *g) {
+    Workspace &w = g->ws;
+    const int sms = sm_count(g);
+    if (g->m > 0)
+        GD_LAUNCH(g, "k_triangles", k_triangles, grid_for(g->m * 32, 256, sms * 16), 256, 0, g->m, g->rp, g->ci,
+                  w.eu, w.ev, w.eslot, w.mate, w.tslot);
     return cudaGetLastError();
 }
 
@@ -814,50 +638,47 @@ cudaError_t run_per_edge_sums(gd_graph *g) {
 static const int TRI_THREADS = 256;
 int32_t tribuf_warps(int sms) { return sms * 8 * (TRI_THREADS / 32); }
 
-size_t cycle_smem_bytes(int32_t cap) { return (size_t)cap * 8 + (size_t)(cap / 2) * 4; }
-
-cudaError_t run_cliques_cycles(gd_graph *g, int variant) {
+// Literal Step 2 (Algorithm 2's CliqueCount and CycleCount per edge).
+cudaError_t run_literal(gd_graph *g) {
     Workspace &w = g->ws;
-    cudaStream_t st = g->stream;
     const int sms = sm_count(g);
-    cudaError_t e;
     if (g->m == 0) return cudaSuccess;
-    e = cudaMemsetAsync(w.cacc, 0, sizeof(uint64_t) * g->nnz, st);
+    cudaError_t e = cudaMemsetAsync(w.cacc, 0, sizeof(uint64_t) * g->nnz, g->stream);
     if (e) return e;
-    e = cudaMemsetAsync(w.yacc, 0, sizeof(uint64_t) * g->nnz, st);
+    e = cudaMemsetAsync(w.yacc, 0, sizeof(uint64_t) * g->nnz, g->stream);
     if (e) return e;
     const int32_t warps = tribuf_warps(sms);
     const int32_t tricap = (int32_t)(w.tribuf_words / ((int64_t)warps * 3));
     const unsigned tri_blocks = (unsigned)(warps / (TRI_THREADS / 32));
-    if (variant == GD_VARIANT_LITERAL) {
-        GD_LAUNCH(g, "k_literal", k_literal, tri_blocks, TRI_THREADS, 0, g->m, g->rp, g->ci, w.eu, w.ev, w.eslot, w.tribuf, tricap,
-                                                      (unsigned long long *)w.cacc, (unsigned long long *)w.yacc,
-                                                      w.status);
-        return cudaGetLastError();
-    }
-    GD_LAUNCH(g, "k_cliques_oriented", k_cliques_oriented, tri_blocks, TRI_THREADS, 0, g->m, g->rp, g->ci, w.eu, w.ev, w.eslot, w.mate,
-                                                           w.tribuf, tricap, (unsigned long long *)w.cacc, w.status);
-    const int32_t cap = g->ctx->opt.smem_table_max;
-    const size_t smem = cycle_smem_bytes(cap);
-    e = cudaFuncSetAttribute(k_cycles_oriented<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e) return e;
-    GD_LAUNCH(g, "k_cycles_smem", k_cycles_oriented<false>, (unsigned)(sms * 2), 256, smem, 
-        g->n, g->rp, g->ci, w.vlist, w.counters, (uint32_t)(cap - 1), nullptr, (unsigned long long *)w.yacc);
-    GD_LAUNCH(g, "k_cycles_global", k_cycles_oriented<true>, (unsigned)w.wtab_ctas, 256, 0, 
-        g->n, g->rp, g->ci, w.vlist, w.counters, 0, w.wtab, (unsigned long long *)w.yacc);
+    GD_LAUNCH(g, "k_literal", k_literal, tri_blocks, TRI_THREADS, 0, g->m, g->rp, g->ci, w.eu, w.ev, w.eslot,
+              w.tribuf, tricap, (unsigned long long *)w.cacc, (unsigned long long *)w.yacc, w.status);
     return cudaGetLastError();
 }
 
-cudaError_t run_final(gd_graph *g, int variant, bool per_edge, uint64_t *out_dev) {
+// 4-clique credits by pairwise tests inside Tri+ (graphs whose largest
+// out-degree exceeds the bitmap kernels' limit).
+cudaError_t run_cliques_pairwise(gd_graph *g) {
     Workspace &w = g->ws;
-    cudaStream_t st = g->stream;
     const int sms = sm_count(g);
-    cudaError_t e = cudaMemsetAsync(w.sums, 0, sizeof(unsigned long long) * 2 * (S_NUM + X_NUM), st);
+    if (g->m == 0) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(w.cacc, 0, sizeof(uint64_t) * g->nnz, g->stream);
     if (e) return e;
+    const int32_t warps = tribuf_warps(sms);
+    const int32_t tricap = (int32_t)(w.tribuf_words / ((int64_t)warps * 3));
+    const unsigned tri_blocks = (unsigned)(warps / (TRI_THREADS / 32));
+    GD_LAUNCH(g, "k_cliques_pairwise", k_cliques_oriented, tri_blocks, TRI_THREADS, 0, g->m, g->rp, g->ci, w.eu,
+              w.ev, w.eslot, w.mate, w.tribuf, tricap, (unsigned long long *)w.cacc, w.status);
+    return cudaGetLastError();
+}
+
+cudaError_t run_final(gd_graph *g, int variant, bool per_edge, bool cliq_credits, uint64_t *out_dev) {
+    Workspace &w = g->ws;
+    const int sms = sm_count(g);
     if (g->m == 0) return cudaSuccess;
     FinalArgs a;
     a.m = g->m; a.n = g->n; a.variant = variant; a.per_edge = per_edge ? 1 : 0;
     a.need_restricted = per_edge ? 1 : 0;
+    a.cliq_credits = cliq_credits ? 1 : 0;
     a.rp = g->rp; a.eu = w.eu; a.ev = w.ev; a.eslot = w.eslot; a.mate = w.mate; a.tslot = w.tslot;
     a.tnode = w.tnode; a.s1 = w.s1; a.au = w.au; a.av = w.av; a.dt = w.dt;
     a.cacc = (const unsigned long long *)w.cacc; a.yacc = (const unsigned long long *)w.yacc;

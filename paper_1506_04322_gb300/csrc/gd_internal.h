@@ -35,6 +35,22 @@ enum SumIdx {
 // Extra sums used only to derive sum cyc_e in the global path.
 enum ExtraIdx { X_T2 = 0, X_C4 = 1, X_NUM = 2 };
 
+// Schedule counters (device word array filled by k_schedule).
+enum CounterIdx {
+    C_SMALL = 0,    // vertices in the shared-memory wedge tier
+    C_MEDIUM = 1,   // vertices in the per-CTA dense-table tier
+    C_MAXDP = 2,    // largest out-degree under the degree ordering
+    C_HUB = 3,      // hubs (whole-GPU batches)
+    C_CL0 = 4,      // 4 clique buckets by out-degree: <=CL_D0, <=CL_D1, <=CL_D2, larger
+    C_DYN = 8,      // dynamic work index of the medium tier
+    C_MB0 = 16,     // medium tier: vertices per log2(wedges) bucket (40 buckets)
+    C_MOFF = 64,    // medium tier: placement offsets per bucket (40)
+    C_NUM = 112
+};
+constexpr int MB_BUCKETS = 40;
+constexpr int CL_D0 = 64, CL_D1 = 256, CL_D2 = 1024;
+constexpr long long HUB_MIN_WEDGES = 1ll << 18;
+
 // Device-side error bits (gdi::Status word).
 enum ErrBits {
     ERR_NEGATIVE = 1,     // a restricted count came out negative: inconsistent input
@@ -59,8 +75,18 @@ struct Workspace {
     uint64_t *cacc = nullptr;      // [nnz] 4-clique credits per slot
     uint64_t *yacc = nullptr;      // [nnz] 4-cycle credits per slot (or cyc_e for literal)
     // schedule
-    int32_t *vlist = nullptr;      // [n] vertices with wedges, small tier then big tier
-    int32_t *counters = nullptr;   // [8] small counters (list sizes, max d+)
+    int32_t *vlist = nullptr;      // [n] small tier from the front, medium tier from the back
+    int32_t *hubs = nullptr;       // [n] hub tier
+    int32_t *clist = nullptr;      // [4n] clique buckets by out-degree
+    int32_t *counters = nullptr;   // [C_NUM]
+    int32_t *nd = nullptr;         // [nnz] degree of each slot's neighbour
+    int32_t *dag_off = nullptr;    // [n+1] out-lists under the degree ordering
+    int32_t *dag_col = nullptr, *dag_slot = nullptr, *dag_nd = nullptr;   // [m]
+    uint32_t *tcred = nullptr;     // [nnz] triangle credits per slot
+    int32_t *touched = nullptr;    // [table slots * n] touched entries of the dense wedge tables
+    int32_t *mlist = nullptr;      // [n] medium tier sorted by decreasing wedge work
+    int64_t *west = nullptr;       // [n] wedge work of medium vertices
+    int32_t *tcount = nullptr;     // [64]
     // scratch
     int32_t *tribuf = nullptr;     // [warps * tricap * 3]
     int64_t tribuf_words = 0;
@@ -135,10 +161,17 @@ void prof_end(gd_ctx *c, cudaStream_t st);
 
 // kernels (gd_count.cu)
 cudaError_t validate_csr(gd_graph *g, int32_t *bad_index_host, int32_t *bad_code_host);
-cudaError_t prepare_edges(gd_graph *g);                   // edge list, mate, T per slot
+cudaError_t prepare_edges(gd_graph *g);                   // edge list, reverse slots, zero sums
+cudaError_t run_triangles_intersect(gd_graph *g);         // |Tri| per slot by intersection
 cudaError_t run_per_edge_sums(gd_graph *g);               // t(x), S1(x), A_u, A_v, D_T
-cudaError_t run_cliques_cycles(gd_graph *g, int variant); // cacc, yacc
-cudaError_t run_final(gd_graph *g, int variant, bool per_edge, uint64_t *out_dev);
+cudaError_t run_literal(gd_graph *g);                     // Algorithm 2 CliqueCount / CycleCount
+cudaError_t run_cliques_pairwise(gd_graph *g);            // 4-clique credits, any out-degree
+cudaError_t run_final(gd_graph *g, int variant, bool per_edge, bool cliq_credits, uint64_t *out_dev);
+// gd_step2.cu
+cudaError_t run_schedule(gd_graph *g, int32_t *counters_host);
+cudaError_t run_triangles_cliques(gd_graph *g, bool per_edge, const int32_t *counters_host);
+cudaError_t run_cycles(gd_graph *g, bool per_edge, const int32_t *counters_host);
+int32_t table_slots(gd_graph *g);
 cudaError_t run_complete(gd_graph *g, int derive_cyc);
 cudaError_t max_degree(gd_graph *g, int32_t *out_host);
 int32_t tribuf_warps(int sms);

@@ -1,0 +1,803 @@
+// gd_step2.cu -- Step 2 of Algorithm 2 (4-cliques and 4-cycles through each
+// edge) and |Tri_e| per edge, organised around the degree ordering
+// a precedes b  <=>  (d_a, a) < (d_b, b).
+//
+// Schedule (per count call, from the CSR):
+//   nd[p]     degree of the neighbour in slot p (rank tests read it coalesced)
+//   N+(a)     out-list of a: neighbours ranked above a, ascending ids, with the
+//             CSR slot of each (a, c) edge.  Under the degree ordering every
+//             out-list has at most sqrt(2|E|) entries.
+//   tiers     vertices by wedge work W(u) = sum_{v in N(u), v below u} d_v.
+//
+// Triangles and 4-cliques ("bitmap" kernels).  For every node a with
+// D = |N+(a)| <= 1024, one CTA builds the adjacency matrix M of the subgraph
+// induced by N+(a) in shared memory, rows and columns in rank order.  For
+// each b in N+(a), S_b = M[b] restricted to ranks above b is Tri+(a,b), the
+// triangles {a, b, c} whose lowest node is a and middle node is b, and every
+// set bit pair {c, d} of S_b joined in M is a 4-clique {a, b, c, d} whose two
+// lowest nodes are a and b.  Each triangle and each 4-clique is therefore
+// found exactly once, and the credits to all its edges are aggregated:
+//   triangle {a,b,c}:  (a,b) += |S_b|, (a,c) += per-c counter, (b,c) += 1
+//   4-clique {a,b,c,d} (a<b<c<d in rank):
+//       (a,b) += |E(S_b)|                           once per (a,b)
+//       (a,c),(a,d) += |M[c] & S_b| summed over b   once per (a,c)
+//       (b,c),(b,d) += |M[c] & S_b|                 once per triangle
+//       (c,d) += |M[c] & M[d] & below(c)|           once per edge inside N+(a)
+// Per-edge |Tri_e| and cliq_e are the sums of the credits of both slots of
+// the edge.  For the global count only the number of 4-cliques is kept.
+//
+// 4-cycles.  Every 4-cycle is counted once from its highest-ranked node u
+// with opposite node y: cnt[y] = number of v below u adjacent to u and y
+// (wedges u-v-y with v, y below u).  Then
+//   global:   4-cycles with top u = sum_y C(cnt[y], 2)
+//   per edge: each wedge carries cnt[y]-1 cycles, credited to (u,v), (v,y).
+// Wedges are walked with a load-balanced warp loop (a warp takes 32
+// neighbours v of u and spreads their lists over its lanes).  Tables:
+//   small  : shared-memory hash per CTA (W(u) <= half its capacity)
+//   medium : dense global table per CTA (1024 threads per vertex)
+//   hubs   : a batch of hubs at a time, every CTA of the GPU working on the
+//            same few dense tables (so they stay in L2), one launch per phase.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "gd_device.cuh"
+#include "gd_internal.h"
+
+namespace gdi {
+
+namespace {
+
+using namespace gdi::dev;
+constexpr unsigned FULL = 0xffffffffu;
+
+// ---------------------------------------------------------------------------
+// schedule
+// ---------------------------------------------------------------------------
+
+__global__ void k_neighbor_degree(int64_t nnz, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                                  int32_t *nd) {
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < nnz; p += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t v = ci[p];
+        nd[p] = rp[v + 1] - rp[v];
+    }
+}
+
+// Per vertex: wedge work, out-degree, tiers.  counters:
+//  [C_SMALL] [C_MEDIUM] [C_MAXDP] [C_HUB] [C_CL0..C_CL3] clique buckets
+__global__ void k_schedule(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                           const int32_t *__restrict__ nd, int64_t small_cap, int64_t hub_min, int32_t cl_max,
+                           int32_t *vlist, int32_t *hubs, int32_t *clist, int32_t *counters, int64_t *dplus,
+                           int64_t *west) {
+    const int lane = lane_id();
+    for (int32_t u = global_warp(); u < n; u += num_warps()) {
+        const int32_t bu = rp[u], du = rp[u + 1] - bu;
+        int64_t est = 0;
+        int32_t dp = 0;
+        for (int32_t i = lane; i < du; i += WARP) {
+            const int32_t v = ci[bu + i], dv = nd[bu + i];
+            if (precedes(dv, v, du, u)) est += dv; else dp++;
+        }
+        est = warp_sum(est);
+        dp = warp_sum(dp);
+        if (lane == 0) {
+            dplus[u] = dp;
+            atomicMax(counters + C_MAXDP, dp);
+            if (est > 0) {
+                if (est <= small_cap) vlist[atomicAdd(counters + C_SMALL, 1)] = u;
+                else if (est <= hub_min) {
+                    vlist[n - 1 - atomicAdd(counters + C_MEDIUM, 1)] = u;
+                    west[u] = est;
+                    atomicAdd(counters + C_MB0 + min(MB_BUCKETS - 1, 63 - __clzll(est)), 1);
+                }
+                else hubs[atomicAdd(counters + C_HUB, 1)] = u;
+            }
+            // clique buckets by out-degree (a node needs 2 out-neighbours to
+            // be the lowest node of a triangle)
+            if (dp >= 2) {
+                const int bkt = dp > cl_max ? 3 : dp <= CL_D0 ? 0 : dp <= CL_D1 ? 1 : 2;
+                const int32_t pos = atomicAdd(counters + C_CL0 + bkt, 1);
+                clist[(int64_t)bkt * n + pos] = u;
+            }
+        }
+    }
+}
+
+__global__ void k_dag_fill(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                           const int32_t *__restrict__ nd, const int32_t *__restrict__ dag_off,
+                           int32_t *dag_col, int32_t *dag_slot, int32_t *dag_nd) {
+    const int lane = lane_id();
+    for (int32_t u = global_warp(); u < n; u += num_warps()) {
+        const int32_t bu = rp[u], du = rp[u + 1] - bu;
+        int32_t o = dag_off[u];
+        for (int32_t i0 = 0; i0 < du; i0 += WARP) {
+            const int32_t i = i0 + lane;
+            bool up = false;
+            int32_t v = 0, dv = 0;
+            if (i < du) {
+                v = ci[bu + i];
+                dv = nd[bu + i];
+                up = precedes(du, u, dv, v);
+            }
+            const unsigned mask = __ballot_sync(FULL, up);
+            if (up) {
+                const int32_t k = o + __popc(mask & ((1u << lane) - 1));
+                dag_col[k] = v; dag_slot[k] = bu + i; dag_nd[k] = dv;
+            }
+            o += __popc(mask);
+        }
+    }
+}
+
+// Medium tier in decreasing order of wedge work (log2 buckets), so that the
+// dynamically scheduled CTAs start the largest vertices first.
+__global__ void k_medium_offsets(int32_t *counters) {
+    if (threadIdx.x != 0) return;
+    int32_t o = 0;
+    for (int b = MB_BUCKETS - 1; b >= 0; b--) { counters[C_MOFF + b] = o; o += counters[C_MB0 + b]; }
+}
+
+__global__ void k_medium_place(int32_t n, const int32_t *__restrict__ vlist, const int64_t *__restrict__ west,
+                               int32_t *counters, int32_t *mlist) {
+    const int32_t nm = counters[C_MEDIUM];
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nm; i += gridDim.x * blockDim.x) {
+        const int32_t u = vlist[n - 1 - i];
+        const int b = min(MB_BUCKETS - 1, 63 - __clzll(west[u]));
+        mlist[atomicAdd(counters + C_MOFF + b, 1)] = u;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// triangles + 4-cliques (bitmap over N+(a))
+// ---------------------------------------------------------------------------
+
+struct CliqueArgs {
+    const int32_t *clist;       // bucket list
+    const int32_t *counters;
+    int bucket;
+    int32_t n;
+    const int32_t *dag_off, *dag_col, *dag_slot, *dag_nd;
+    unsigned long long *cacc;   // per-slot clique credits (per-edge mode)
+    uint32_t *tcred;            // per-slot triangle credits
+    unsigned long long *sums;   // u128 sums (S_CLIQ gets 6 * K4 in global mode)
+    int32_t *status;            // error bits
+};
+
+template <int DMAX>
+struct CliqueSmem {
+    static constexpr int W = DMAX / 32;
+    int32_t ids[DMAX];          // N+(a), ascending ids
+    int32_t degs[DMAX];         // their degrees
+    int32_t rank_of[DMAX];      // rank index of ids[k] within N+(a)
+    int32_t rid[DMAX], rslot[DMAX], rdeg[DMAX];   // by rank index
+    uint32_t cnt_p[DMAX], tri_p[DMAX];
+    uint32_t M[DMAX * W];       // adjacency, row r = node of rank index r
+};
+
+template <int DMAX, int THREADS, bool CREDIT>
+__global__ void __launch_bounds__(THREADS)
+k_clique_bitmap(CliqueArgs a) {
+    constexpr int W = DMAX / 32;
+    constexpr int NW = THREADS / 32;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    CliqueSmem<DMAX> &S = *reinterpret_cast<CliqueSmem<DMAX> *>(smraw);
+    uint32_t *Sbuf = reinterpret_cast<uint32_t *>(smraw + sizeof(CliqueSmem<DMAX>));   // [NW][W]
+    const int lane = lane_id(), warp = threadIdx.x >> 5;
+    const int32_t nv = a.counters[C_CL0 + a.bucket];
+    const int32_t *list = a.clist + (int64_t)a.bucket * a.n;
+    unsigned long long k4_local = 0;
+    uint32_t *mys = Sbuf + warp * W;
+
+    for (int32_t idx = blockIdx.x; idx < nv; idx += gridDim.x) {
+        const int32_t va = list[idx];
+        const int32_t off = a.dag_off[va], D = a.dag_off[va + 1] - off;
+        const int Wd = (D + 31) >> 5;
+        for (int k = threadIdx.x; k < D; k += THREADS) { S.ids[k] = a.dag_col[off + k]; S.degs[k] = a.dag_nd[off + k]; }
+        for (int k = threadIdx.x; k < D * Wd; k += THREADS) S.M[k] = 0;
+        for (int k = threadIdx.x; k < D; k += THREADS) { S.cnt_p[k] = 0; S.tri_p[k] = 0; }
+        __syncthreads();
+        // rank index of each out-neighbour (number of out-neighbours below it)
+        for (int k = threadIdx.x; k < D; k += THREADS) {
+            const int32_t dk = S.degs[k], ik = S.ids[k];
+            int32_t r = 0;
+            for (int j = 0; j < D; j++) r += precedes(S.degs[j], S.ids[j], dk, ik);
+            S.rank_of[k] = r;
+            S.rid[r] = ik; S.rslot[r] = a.dag_slot[off + k]; S.rdeg[r] = dk;
+        }
+        __syncthreads();
+        // adjacency inside N+(a): for c in N+(a), every x in N+(c) that is in N+(a)
+        for (int k = warp; k < D; k += NW) {
+            const int32_t c = S.ids[k], rc = S.rank_of[k];
+            const int32_t co = a.dag_off[c], cd = a.dag_off[c + 1] - co;
+            for (int32_t t = lane; t < cd; t += WARP) {
+                const int32_t x = a.dag_col[co + t];
+                int32_t lo = 0, hi = D;
+                while (lo < hi) { const int32_t mid = (lo + hi) >> 1; if (S.ids[mid] < x) lo = mid + 1; else hi = mid; }
+                if (lo < D && S.ids[lo] == x) {
+                    const int32_t rx = S.rank_of[lo];
+                    atomicOr(&S.M[rc * Wd + (rx >> 5)], 1u << (rx & 31));
+                    atomicOr(&S.M[rx * Wd + (rc >> 5)], 1u << (rc & 31));
+                }
+            }
+        }
+        __syncthreads();
+        // for each b (rank index rb): S_b = M[rb] & ranks above rb
+        for (int rb = warp; rb < D; rb += NW) {
+            uint32_t nS = 0;
+            for (int w = lane; w < Wd; w += WARP) {
+                uint32_t x = S.M[rb * Wd + w];
+                const int lo = rb + 1;   // keep ranks >= lo
+                if (w * 32 + 31 < lo) x = 0;
+                else if (w * 32 < lo) x &= ~((1u << (lo - w * 32)) - 1u);
+                mys[w] = x;
+                nS += __popc(x);
+            }
+            nS = warp_sum(nS);
+            __syncwarp();
+            if (nS == 0) continue;
+            const int32_t b = S.rid[rb];
+            const int32_t bo = a.dag_off[b], bd = a.dag_off[b + 1] - bo;
+            unsigned long long k2 = 0;   // ordered adjacent pairs inside S_b
+            for (int q = rb + 1 + lane; q < D; q += WARP) {
+                if (!((mys[q >> 5] >> (q & 31)) & 1u)) continue;
+                uint32_t kq = 0;
+                for (int w = 0; w < Wd; w++) kq += __popc(S.M[q * Wd + w] & mys[w]);
+                k2 += kq;
+                atomicAdd(&S.tri_p[q], 1u);
+                if (CREDIT) atomicAdd(&S.cnt_p[q], kq);
+                // slot of (b, c_q): c_q is in N+(b)
+                const int32_t cq = S.rid[q];
+                int32_t lo = 0, hi = bd;
+                while (lo < hi) { const int32_t mid = (lo + hi) >> 1; if (ldg(a.dag_col + bo + mid) < cq) lo = mid + 1; else hi = mid; }
+                if (lo >= bd || ldg(a.dag_col + bo + lo) != cq) { atomicOr(a.status, ERR_CAPACITY); continue; }
+                const int32_t sbc = ldg(a.dag_slot + bo + lo);
+                atomicAdd(a.tcred + sbc, 1u);
+                if (CREDIT && kq) atomicAdd(a.cacc + sbc, (unsigned long long)kq);
+            }
+            k2 = warp_sum(k2);
+            if (lane == 0) {
+                atomicAdd(a.tcred + S.rslot[rb], nS);
+                if (CREDIT && k2) atomicAdd(a.cacc + S.rslot[rb], k2 >> 1);
+                k4_local += k2 >> 1;
+            }
+            __syncwarp();
+        }
+        __syncthreads();
+        // per-node credits of (a, c) and pair credits of edges (c, d) inside N+(a)
+        for (int q = threadIdx.x; q < D; q += THREADS) {
+            if (S.tri_p[q]) atomicAdd(a.tcred + S.rslot[q], S.tri_p[q]);
+            if (CREDIT && S.cnt_p[q]) atomicAdd(a.cacc + S.rslot[q], (unsigned long long)S.cnt_p[q]);
+        }
+        if (CREDIT) {
+            for (int p = warp; p < D; p += NW) {
+                const int32_t cp = S.rid[p];
+                const int32_t po = a.dag_off[cp], pd = a.dag_off[cp + 1] - po;
+                const int pw = p >> 5;
+                for (int q = p + 1 + lane; q < D; q += WARP) {
+                    if (!((S.M[p * Wd + (q >> 5)] >> (q & 31)) & 1u)) continue;
+                    uint32_t pc = 0;
+                    for (int w = 0; w < pw; w++) pc += __popc(S.M[p * Wd + w] & S.M[q * Wd + w]);
+                    if (p & 31) pc += __popc(S.M[p * Wd + pw] & S.M[q * Wd + pw] & ((1u << (p & 31)) - 1u));
+                    if (!pc) continue;
+                    // c_p ranks below c_q, so c_q is in N+(c_p)
+                    const int32_t cq = S.rid[q];
+                    int32_t lo = 0, hi = pd;
+                    while (lo < hi) { const int32_t mid = (lo + hi) >> 1; if (ldg(a.dag_col + po + mid) < cq) lo = mid + 1; else hi = mid; }
+                    if (lo >= pd || ldg(a.dag_col + po + lo) != cq) { atomicOr(a.status, ERR_CAPACITY); continue; }
+                    atomicAdd(a.cacc + ldg(a.dag_slot + po + lo), (unsigned long long)pc);
+                }
+            }
+        }
+        __syncthreads();
+    }
+    if (!CREDIT) {
+        __shared__ unsigned long long red[NW];
+        const unsigned long long x = warp_sum(k4_local);
+        if (lane == 0) red[warp] = x;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            unsigned long long s = 0;
+            for (int w = 0; w < NW; w++) s += red[w];
+            add_u128(a.sums + 2 * S_CLIQ, 6ull * s);   // sum_e cliq_e = 6 f41
+        }
+    }
+}
+
+// |Tri_e| of both slots of every edge from the triangle credits
+__global__ void k_tri_symmetrize(int64_t m, const int32_t *__restrict__ eslot, const int32_t *__restrict__ mate,
+                                 const uint32_t *__restrict__ tcred, uint32_t *tslot) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < m; k += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t p = eslot[k], q = mate[p];
+        const uint32_t t = tcred[p] + tcred[q];
+        tslot[p] = t;
+        tslot[q] = t;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// 4-cycles
+// ---------------------------------------------------------------------------
+
+// Load-balanced walk over the wedges (u, v, y), v and y below u, for the
+// neighbours of u at positions [i0, i1) taken 32 at a time by one warp.
+// f(item_lane, slot_vy, y) is called for every wedge; item_lane is the lane
+// that loaded v (slot of (u, v) = bu + it + item_lane).  done(it) is called
+// by the whole warp after each group of 32 neighbours.
+template <class F, class G>
+__device__ __forceinline__ void warp_wedges(int32_t u, int32_t du, int32_t bu, int32_t i0, int32_t i1,
+                                            int32_t istep, const int32_t *__restrict__ rp,
+                                            const int32_t *__restrict__ ci, const int32_t *__restrict__ nd,
+                                            F f, G done) {
+    const int lane = lane_id();
+    for (int32_t it = i0; it < i1; it += istep) {
+        const int32_t i = it + lane;
+        int32_t len = 0, start = 0;
+        if (i < i1 && i < it + WARP) {
+            const int32_t v = ci[bu + i], dv = nd[bu + i];
+            if (precedes(dv, v, du, u)) { len = dv; start = rp[v]; }
+        }
+        const int32_t incl = warp_incl_scan(len);
+        const int32_t total = __shfl_sync(FULL, incl, 31);
+        const int32_t excl = incl - len;
+        for (int32_t w0 = 0; w0 < total; w0 += WARP) {
+            const int32_t w = w0 + lane;
+            int32_t k = 0;
+#pragma unroll
+            for (int s = 16; s >= 1; s >>= 1) {
+                const int32_t e = __shfl_sync(FULL, excl, k + s);
+                if (e <= w) k += s;
+            }
+            const int32_t ks = __shfl_sync(FULL, start, k);
+            const int32_t ke = __shfl_sync(FULL, excl, k);
+            bool ok = false;
+            const bool live = w < total;
+            int32_t q = 0, y = 0;
+            if (live) {
+                q = ks + (w - ke);
+                y = ci[q];
+                ok = precedes(nd[q], y, du, u);
+            }
+            // called by every lane: ok says whether (k, q, y) is a wedge, live
+            // whether the lane lies inside this group's wedge range
+            f(k, q, y, ok, live);
+        }
+        done(it);
+    }
+}
+
+// Per-item sums inside warp_wedges: the in-range lanes of one inner
+// iteration hold wedges of non-decreasing items k, each item on a contiguous
+// run of lanes, so a segmented warp scan leaves the last lane of each run to
+// add the run's sum to the item accumulator.  Lanes past the end of the
+// group (live == false) form runs of their own and add nothing.
+__device__ __forceinline__ void item_add(unsigned long long *item, int k, unsigned long long x, bool live) {
+    const int lane = lane_id();
+    const int kk = live ? k : -1 - lane;
+    unsigned long long s = live ? x : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long y = __shfl_up_sync(FULL, s, o);
+        const int ky = __shfl_up_sync(FULL, kk, o);
+        if (lane >= o && ky == kk) s += y;
+    }
+    const int knext = __shfl_down_sync(FULL, kk, 1);
+    const bool tail = (lane == 31) || (knext != kk);
+    if (live && tail && s) atomicAdd(item + k, s);
+}
+
+// shared-memory hash (keys -1 = empty); at most cap/2 distinct keys
+__device__ __forceinline__ uint32_t sm_find(const int32_t *keys, const uint32_t *vals, uint32_t capmask, int32_t y) {
+    uint32_t h = hash32((uint32_t)y) & capmask;
+    for (uint32_t probes = 0; probes <= capmask; probes++) {
+        const int32_t k = keys[h];
+        if (k == y) return vals[h];
+        if (k == -1) return 0;
+        h = (h + 1) & capmask;
+    }
+    return 0;
+}
+
+struct CycleArgs {
+    int32_t n;
+    const int32_t *rp, *ci, *nd;
+    const int32_t *vlist, *hubs, *mlist;
+    int32_t *counters;           // counters[C_DYN] is the medium tier's work index
+    uint32_t capmask;
+    uint32_t *tables;            // [slots][n] dense counters, zero at rest
+    int32_t *touched;            // [slots][n]
+    int32_t *tcount;             // [slots]
+    unsigned long long *yacc;    // per-slot 4-cycle credits (per-edge mode)
+    unsigned long long *sums;    // u128 sums: X_C4 gets sum_e C4(e) = 4 * 4-cycles (global mode)
+    int32_t hub0, nhub;          // hub batch
+};
+
+__device__ __forceinline__ unsigned long long c2(uint32_t c) { return (unsigned long long)c * (c - 1) / 2; }
+
+template <int THREADS, bool CREDIT>
+__global__ void __launch_bounds__(THREADS)
+k_cycles_small(CycleArgs a) {
+    constexpr int NW = THREADS / 32;
+    extern __shared__ __align__(16) int32_t sm[];
+    __shared__ int32_t ntouched;
+    __shared__ unsigned long long item[NW][WARP];
+    int32_t *keys = sm;
+    uint32_t *vals = (uint32_t *)(sm + (a.capmask + 1));
+    int32_t *touched = sm + 2 * (a.capmask + 1);
+    const int lane = lane_id(), warp = threadIdx.x >> 5;
+    const int32_t nv = a.counters[C_SMALL];
+    for (uint32_t i = threadIdx.x; i <= a.capmask; i += THREADS) { keys[i] = -1; vals[i] = 0; }
+    if (threadIdx.x == 0) ntouched = 0;
+    item[warp][lane] = 0;
+    unsigned long long c4 = 0;
+    __syncthreads();
+    for (int32_t idx = blockIdx.x; idx < nv; idx += gridDim.x) {
+        const int32_t u = a.vlist[idx];
+        const int32_t bu = a.rp[u], du = a.rp[u + 1] - bu;
+        warp_wedges(u, du, bu, warp * WARP, du, NW * WARP, a.rp, a.ci, a.nd,
+            [&](int k, int32_t q, int32_t y, bool ok, bool live) {
+                if (!ok) return;
+                uint32_t h = hash32((uint32_t)y) & a.capmask;
+                uint32_t old = 0;
+                while (true) {
+                    const int32_t kk = keys[h];
+                    if (kk == y) { old = atomicAdd(vals + h, 1u); break; }
+                    if (kk == -1) {
+                        const int32_t prev = atomicCAS(keys + h, -1, y);
+                        if (prev == -1) { old = atomicAdd(vals + h, 1u); touched[atomicAdd(&ntouched, 1)] = (int32_t)h; break; }
+                        if (prev == y) { old = atomicAdd(vals + h, 1u); break; }
+                    }
+                    h = (h + 1) & a.capmask;
+                }
+                if (!CREDIT) c4 += old;
+            },
+            [&](int32_t) {});
+        __syncthreads();
+        if (CREDIT) {
+            warp_wedges(u, du, bu, warp * WARP, du, NW * WARP, a.rp, a.ci, a.nd,
+                [&](int k, int32_t q, int32_t y, bool ok, bool live) {
+                    const uint32_t c = ok ? sm_find(keys, vals, a.capmask, y) : 0;
+                    if (c > 1) atomicAdd(a.yacc + q, (unsigned long long)(c - 1));
+                    item_add(item[warp], k, c > 1 ? c - 1 : 0, live);
+                },
+                [&](int32_t it) {
+                    __syncwarp();
+                    const unsigned long long s = item[warp][lane];
+                    if (s) { atomicAdd(a.yacc + bu + it + lane, s); item[warp][lane] = 0; }
+                    __syncwarp();
+                });
+            __syncthreads();
+        }
+        const int32_t nt = ntouched;
+        for (int32_t i = threadIdx.x; i < nt; i += THREADS) {
+            const int32_t h = touched[i];
+            keys[h] = -1; vals[h] = 0;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) ntouched = 0;
+        __syncthreads();
+    }
+    if (!CREDIT) {
+        c4 = warp_sum(c4);
+        if (lane == 0) add_u128(a.sums + 2 * (S_NUM + X_C4), 4 * c4);
+    }
+}
+
+// Medium tier: one vertex per CTA at a time, dense global table per CTA.
+template <int THREADS, bool CREDIT>
+__global__ void __launch_bounds__(THREADS)
+k_cycles_medium(CycleArgs a) {
+    constexpr int NW = THREADS / 32;
+    __shared__ int32_t ntouched;
+    __shared__ unsigned long long item[NW][WARP];
+    const int lane = lane_id(), warp = threadIdx.x >> 5;
+    __shared__ int32_t next;
+    const int32_t nv = a.counters[C_MEDIUM];
+    uint32_t *tab = a.tables + (int64_t)blockIdx.x * a.n;
+    int32_t *tl = a.touched + (int64_t)blockIdx.x * a.n;
+    if (threadIdx.x == 0) { ntouched = 0; next = atomicAdd(a.counters + C_DYN, 1); }
+    item[warp][lane] = 0;
+    unsigned long long c4 = 0;
+    __syncthreads();
+    while (true) {
+        const int32_t idx = next;
+        if (idx >= nv) break;
+        const int32_t u = a.mlist[idx];
+        const int32_t bu = a.rp[u], du = a.rp[u + 1] - bu;
+        warp_wedges(u, du, bu, warp * WARP, du, NW * WARP, a.rp, a.ci, a.nd,
+            [&](int k, int32_t q, int32_t y, bool ok, bool live) {
+                // the values returned by the increments of y sum to C(cnt[y], 2)
+                const uint32_t old = ok ? atomicAdd(tab + y, 1u) : 1u;
+                if (!CREDIT && ok) c4 += old;
+                const bool first = ok && old == 0;
+                const unsigned fm = __ballot_sync(FULL, first);
+                if (fm) {
+                    int32_t base = 0;
+                    if (lane == __ffs(fm) - 1) base = atomicAdd(&ntouched, __popc(fm));
+                    base = __shfl_sync(FULL, base, __ffs(fm) - 1);
+                    if (first) tl[base + __popc(fm & ((1u << lane) - 1))] = y;
+                }
+            },
+            [&](int32_t) {});
+        __syncthreads();
+        if (CREDIT) {
+            warp_wedges(u, du, bu, warp * WARP, du, NW * WARP, a.rp, a.ci, a.nd,
+                [&](int k, int32_t q, int32_t y, bool ok, bool live) {
+                    const uint32_t c = ok ? __ldcg(tab + y) : 0;
+                    if (c > 1) atomicAdd(a.yacc + q, (unsigned long long)(c - 1));
+                    item_add(item[warp], k, c > 1 ? c - 1 : 0, live);
+                },
+                [&](int32_t it) {
+                    __syncwarp();
+                    const unsigned long long s = item[warp][lane];
+                    if (s) { atomicAdd(a.yacc + bu + it + lane, s); item[warp][lane] = 0; }
+                    __syncwarp();
+                });
+            __syncthreads();
+        }
+        const int32_t nt = ntouched;
+        for (int32_t i = threadIdx.x; i < nt; i += THREADS) tab[tl[i]] = 0;
+        __syncthreads();
+        if (threadIdx.x == 0) { ntouched = 0; next = atomicAdd(a.counters + C_DYN, 1); }
+        __syncthreads();
+    }
+    if (!CREDIT) {
+        c4 = warp_sum(c4);
+        if (lane == 0) add_u128(a.sums + 2 * (S_NUM + X_C4), 4 * c4);
+    }
+}
+
+// Hub tier, phase PH (0 count, 1 credit): every warp of the grid takes groups
+// of 32 neighbours of the hubs hub0 .. hub0+nhub-1; hub h uses table h.
+template <int PH>
+__global__ void __launch_bounds__(256)
+k_cycles_hub(CycleArgs a) {
+    __shared__ unsigned long long item[8][WARP];
+    const int lane = lane_id(), warp = threadIdx.x >> 5;
+    item[warp][lane] = 0;
+    __syncwarp();
+    // units: (hub h, group g of 32 neighbours)
+    int64_t units = 0;
+    for (int h = 0; h < a.nhub; h++) {
+        const int32_t u = a.hubs[a.hub0 + h];
+        units += (a.rp[u + 1] - a.rp[u] + WARP - 1) / WARP;
+    }
+    for (int64_t unit = global_warp(); unit < units; unit += num_warps()) {
+        int h = 0;
+        int64_t rem = unit;
+        int32_t u = 0, bu = 0, du = 0;
+        for (; h < a.nhub; h++) {
+            u = a.hubs[a.hub0 + h];
+            bu = a.rp[u]; du = a.rp[u + 1] - bu;
+            const int64_t g = (du + WARP - 1) / WARP;
+            if (rem < g) break;
+            rem -= g;
+        }
+        uint32_t *tab = a.tables + (int64_t)h * a.n;
+        const int32_t i0 = (int32_t)rem * WARP;
+        const int32_t i1 = min(du, i0 + WARP);
+        if (PH == 0) {
+            warp_wedges(u, du, bu, i0, i1, WARP, a.rp, a.ci, a.nd,
+                [&](int k, int32_t q, int32_t y, bool ok, bool live) {
+                    if (ok) atomicAdd(tab + y, 1u);      // result unused: a reduction
+                },
+                [&](int32_t) {});
+        } else {
+            warp_wedges(u, du, bu, i0, i1, WARP, a.rp, a.ci, a.nd,
+                [&](int k, int32_t q, int32_t y, bool ok, bool live) {
+                    const uint32_t c = ok ? __ldcg(tab + y) : 0;
+                    if (c > 1) atomicAdd(a.yacc + q, (unsigned long long)(c - 1));
+                    item_add(item[warp], k, c > 1 ? c - 1 : 0, live);
+                },
+                [&](int32_t it) {
+                    __syncwarp();
+                    const unsigned long long s = item[warp][lane];
+                    if (s) { atomicAdd(a.yacc + bu + it + lane, s); item[warp][lane] = 0; }
+                    __syncwarp();
+                });
+        }
+    }
+}
+
+// Hub tier, last phase: clear the batch's tables by a full scan (a hub
+// touches a large part of its table) and sum C(cnt,2) when counting globally.
+template <bool CREDIT>
+__global__ void k_cycles_hub_clear(CycleArgs a) {
+    unsigned long long c4 = 0;
+    const int64_t total = (int64_t)a.nhub * a.n;
+    const int64_t total4 = total >> 2;
+    uint4 *t4 = reinterpret_cast<uint4 *>(a.tables);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total4; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint4 v = t4[i];
+        if (v.x | v.y | v.z | v.w) {
+            if (!CREDIT) c4 += c2(v.x) + c2(v.y) + c2(v.z) + c2(v.w);
+            t4[i] = make_uint4(0, 0, 0, 0);
+        }
+    }
+    for (int64_t i = (total4 << 2) + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t v = a.tables[i];
+        if (v) {
+            if (!CREDIT) c4 += c2(v);
+            a.tables[i] = 0;
+        }
+    }
+    if (!CREDIT) {
+        c4 = warp_sum(c4);
+        if (lane_id() == 0) add_u128(a.sums + 2 * (S_NUM + X_C4), 4 * c4);
+    }
+}
+
+__global__ void k_zero_i32(int32_t *p, int32_t k) {
+    for (int32_t i = threadIdx.x; i < k; i += blockDim.x) p[i] = 0;
+}
+
+inline unsigned grid_for(int64_t items, int per_block, int max_blocks) {
+    int64_t b = (items + per_block - 1) / per_block;
+    if (b < 1) b = 1;
+    if (b > max_blocks) b = max_blocks;
+    return (unsigned)b;
+}
+
+template <typename K>
+cudaError_t allow_smem(K kernel, size_t bytes) {
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+}  // namespace
+
+// ===========================================================================
+// host launchers
+// ===========================================================================
+
+static int sms_of(gd_graph *g) { return g->ctx->num_sms > 0 ? g->ctx->num_sms : 152; }
+
+cudaError_t exclusive_scan_i64(gd_graph *g, const int64_t *in, int64_t *out, int64_t len, int64_t *tmp);
+
+__global__ void k_narrow_i32(const int64_t *in, int32_t *out, int64_t len) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < len; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = (int32_t)in[i];
+}
+
+// nd, tiers, out-lists.  Reads the counters back (one synchronization).
+cudaError_t run_schedule(gd_graph *g, int32_t *counters_host) {
+    Workspace &w = g->ws;
+    const int sms = sms_of(g);
+    const int32_t n = g->n;
+    cudaError_t e = cudaMemsetAsync(w.counters, 0, C_NUM * sizeof(int32_t), g->stream);
+    if (e) return e;
+    if (n > 0 && g->nnz > 0) {
+        GD_LAUNCH(g, "k_neighbor_degree", k_neighbor_degree, grid_for(g->nnz, 256, sms * 16), 256, 0,
+                  g->nnz, g->rp, g->ci, w.nd);
+        const int64_t small_cap = g->ctx->opt.smem_table_max / 2;
+        GD_LAUNCH(g, "k_schedule", k_schedule, grid_for((int64_t)n * 32, 256, sms * 16), 256, 0,
+                  n, g->rp, g->ci, w.nd, small_cap, (int64_t)1 << g->ctx->opt.hub_wedges_log2,
+                  g->ctx->opt.bitmap_max_outdeg, w.vlist, w.hubs, w.clist, w.counters, w.scan_tmp, w.west);
+        GD_LAUNCH(g, "k_medium_offsets", k_medium_offsets, 1, 32, 0, w.counters);
+        GD_LAUNCH(g, "k_medium_place", k_medium_place, grid_for(n, 256, sms * 4), 256, 0, n, w.vlist, w.west,
+                  w.counters, w.mlist);
+        int64_t *offs = w.scan_tmp + (n + 1);
+        int64_t *tmp = w.scan_tmp + 2 * (int64_t)(n + 1);
+        e = exclusive_scan_i64(g, w.scan_tmp, offs, n, tmp);
+        if (e) return e;
+        GD_LAUNCH(g, "k_narrow", k_narrow_i32, grid_for(n + 1, 256, sms * 8), 256, 0, offs, w.dag_off, n + 1);
+        GD_LAUNCH(g, "k_dag_fill", k_dag_fill, grid_for((int64_t)n * 32, 256, sms * 16), 256, 0,
+                  n, g->rp, g->ci, w.nd, w.dag_off, w.dag_col, w.dag_slot, w.dag_nd);
+    }
+    e = cudaMemcpyAsync(counters_host, w.counters, C_NUM * sizeof(int32_t), cudaMemcpyDeviceToHost, g->stream);
+    if (e) return e;
+    e = cudaStreamSynchronize(g->stream);
+    if (e) return e;
+    return cudaGetLastError();
+}
+
+size_t clique_smem_bytes(int dmax, int threads) {
+    const int W = dmax / 32;
+    return (size_t)dmax * 4 * 7 + (size_t)dmax * W * 4 + (size_t)(threads / 32) * W * 4 + 64;
+}
+
+template <int DMAX, int THREADS, bool CREDIT>
+static cudaError_t launch_clique(gd_graph *g, int bucket, int count) {
+    if (count == 0) return cudaSuccess;
+    Workspace &w = g->ws;
+    CliqueArgs a;
+    a.clist = w.clist; a.counters = w.counters; a.bucket = bucket; a.n = g->n;
+    a.dag_off = w.dag_off; a.dag_col = w.dag_col; a.dag_slot = w.dag_slot; a.dag_nd = w.dag_nd;
+    a.cacc = (unsigned long long *)w.cacc; a.tcred = w.tcred; a.sums = w.sums; a.status = w.status;
+    const size_t smem = sizeof(CliqueSmem<DMAX>) + (size_t)(THREADS / 32) * (DMAX / 32) * 4;
+    cudaError_t e = allow_smem(k_clique_bitmap<DMAX, THREADS, CREDIT>, smem);
+    if (e) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_clique_bitmap<DMAX, THREADS, CREDIT>, THREADS, smem);
+    if (e) return e;
+    const unsigned grid = grid_for(count, 1, sms_of(g) * (per_sm > 0 ? per_sm : 1));
+    GD_LAUNCH(g, "k_clique_bitmap", (k_clique_bitmap<DMAX, THREADS, CREDIT>), grid, THREADS, smem, a);
+    return cudaGetLastError();
+}
+
+// Triangles per slot and 4-cliques (credits when per_edge).  Requires the
+// largest out-degree <= CL_D2 (checked by the caller).
+cudaError_t run_triangles_cliques(gd_graph *g, bool per_edge, const int32_t *cnt) {
+    Workspace &w = g->ws;
+    const int sms = sms_of(g);
+    if (g->m == 0) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(w.tcred, 0, sizeof(uint32_t) * g->nnz, g->stream);
+    if (e) return e;
+    if (per_edge) {
+        e = cudaMemsetAsync(w.cacc, 0, sizeof(uint64_t) * g->nnz, g->stream);
+        if (e) return e;
+        if ((e = launch_clique<CL_D0, 32, true>(g, 0, cnt[C_CL0]))) return e;
+        if ((e = launch_clique<CL_D1, 128, true>(g, 1, cnt[C_CL0 + 1]))) return e;
+        if ((e = launch_clique<CL_D2, 512, true>(g, 2, cnt[C_CL0 + 2]))) return e;
+    } else {
+        if ((e = launch_clique<CL_D0, 32, false>(g, 0, cnt[C_CL0]))) return e;
+        if ((e = launch_clique<CL_D1, 128, false>(g, 1, cnt[C_CL0 + 1]))) return e;
+        if ((e = launch_clique<CL_D2, 512, false>(g, 2, cnt[C_CL0 + 2]))) return e;
+    }
+    GD_LAUNCH(g, "k_tri_symmetrize", k_tri_symmetrize, grid_for(g->m, 256, sms * 8), 256, 0,
+              g->m, w.eslot, w.mate, w.tcred, w.tslot);
+    return cudaGetLastError();
+}
+
+int32_t hub_batch(gd_graph *g) {
+    // a few dense tables at a time so that they stay resident in L2 (~64 MB)
+    const int64_t per = 4 * (int64_t)(g->n > 0 ? g->n : 1);
+    int64_t b = (64ll << 20) / per;
+    if (b < 1) b = 1;
+    if (b > 16) b = 16;
+    return (int32_t)b;
+}
+
+int32_t table_slots(gd_graph *g) {
+    const int32_t s = 2 * sms_of(g);
+    const int32_t b = hub_batch(g);
+    return s > b ? s : b;
+}
+
+// 4-cycles: credits (per_edge) or the 4-cycle total (global).
+cudaError_t run_cycles(gd_graph *g, bool per_edge, const int32_t *cnt) {
+    Workspace &w = g->ws;
+    const int sms = sms_of(g);
+    if (g->m == 0) return cudaSuccess;
+    cudaError_t e;
+    if (per_edge) {
+        e = cudaMemsetAsync(w.yacc, 0, sizeof(uint64_t) * g->nnz, g->stream);
+        if (e) return e;
+    }
+    CycleArgs a;
+    a.n = g->n; a.rp = g->rp; a.ci = g->ci; a.nd = w.nd;
+    a.vlist = w.vlist; a.hubs = w.hubs; a.mlist = w.mlist; a.counters = w.counters;
+    a.capmask = (uint32_t)(g->ctx->opt.smem_table_max - 1);
+    a.tables = w.wtab; a.touched = w.touched; a.tcount = w.tcount;
+    a.yacc = (unsigned long long *)w.yacc; a.sums = w.sums;
+    a.hub0 = 0; a.nhub = 0;
+    // hubs, in batches
+    const int32_t nh = cnt[C_HUB], B = hub_batch(g);
+    for (int32_t h0 = 0; h0 < nh; h0 += B) {
+        a.hub0 = h0;
+        a.nhub = nh - h0 < B ? nh - h0 : B;
+        GD_LAUNCH(g, "k_cycles_hub_count", k_cycles_hub<0>, (unsigned)(sms * 8), 256, 0, a);
+        if (per_edge) GD_LAUNCH(g, "k_cycles_hub_credit", k_cycles_hub<1>, (unsigned)(sms * 8), 256, 0, a);
+        if (per_edge) GD_LAUNCH(g, "k_cycles_hub_clear", k_cycles_hub_clear<true>, (unsigned)(sms * 4), 256, 0, a);
+        else GD_LAUNCH(g, "k_cycles_hub_clear", k_cycles_hub_clear<false>, (unsigned)(sms * 4), 256, 0, a);
+    }
+    // medium tier
+    if (cnt[C_MEDIUM] > 0) {
+        const int32_t slots = 2 * sms;    // two 1024-thread CTAs fit on an SM
+        const unsigned grid = (unsigned)(cnt[C_MEDIUM] < slots ? cnt[C_MEDIUM] : slots);
+        if (per_edge) GD_LAUNCH(g, "k_cycles_medium", (k_cycles_medium<1024, true>), grid, 1024, 0, a);
+        else GD_LAUNCH(g, "k_cycles_medium", (k_cycles_medium<1024, false>), grid, 1024, 0, a);
+    }
+    // small tier
+    if (cnt[C_SMALL] > 0) {
+        const size_t smem = (size_t)(a.capmask + 1) * 8 + (size_t)((a.capmask + 1) / 2) * 4;
+        if (per_edge) {
+            if ((e = allow_smem(k_cycles_small<256, true>, smem))) return e;
+            GD_LAUNCH(g, "k_cycles_small", (k_cycles_small<256, true>), (unsigned)(sms * 2), 256, smem, a);
+        } else {
+            if ((e = allow_smem(k_cycles_small<256, false>, smem))) return e;
+            GD_LAUNCH(g, "k_cycles_small", (k_cycles_small<256, false>), (unsigned)(sms * 2), 256, smem, a);
+        }
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace gdi

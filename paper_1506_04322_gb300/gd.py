@@ -54,7 +54,8 @@ class gd_stage_stat(ctypes.Structure):
 class gd_options(ctypes.Structure):
     _fields_ = [("variant", ctypes.c_int32), ("block_threads", ctypes.c_int32),
                 ("ctas_per_sm", ctypes.c_int32), ("smem_table_max", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 8)]
+                ("bitmap_max_outdeg", ctypes.c_int32), ("hub_wedges_log2", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 6)]
 
 
 _lib = None
@@ -245,11 +246,16 @@ class Context:
     """A libgd context on one GPU."""
 
     def __init__(self, device: int = 0, hbm_budget_bytes: int = 0, variant: int = GD_VARIANT_AUTO,
-                 smem_table_max: int | None = None):
+                 smem_table_max: int | None = None, bitmap_max_outdeg: int | None = None,
+                 hub_wedges_log2: int | None = None):
         o = gd_default_options()
         o.variant = variant
         if smem_table_max:
             o.smem_table_max = smem_table_max
+        if bitmap_max_outdeg:
+            o.bitmap_max_outdeg = bitmap_max_outdeg
+        if hub_wedges_log2:
+            o.hub_wedges_log2 = hub_wedges_log2
         self.handle = gd_init(device, hbm_budget_bytes, o)
         self._graphs = []
 

@@ -26,6 +26,10 @@ def ctxs():
     # a context whose shared-memory wedge table is tiny, so the global-table
     # tier of the 4-cycle kernel runs on small graphs too
     out["tiny_table"] = gd.Context(0, variant=gd.GD_VARIANT_ORIENTED, smem_table_max=256)
+    # every scheduling tier on small graphs: hub batches from 2^6 wedges, and
+    # the pairwise 4-clique path for out-degrees above 8
+    out["all_tiers"] = gd.Context(0, variant=gd.GD_VARIANT_ORIENTED, smem_table_max=256,
+                                  bitmap_max_outdeg=8, hub_wedges_log2=6)
     yield out
     for c in out.values():
         c.close()
@@ -64,7 +68,7 @@ def structured_graphs():
     return gs
 
 
-@pytest.mark.parametrize("variant", VARIANTS + ["tiny_table"])
+@pytest.mark.parametrize("variant", VARIANTS + ["tiny_table", "all_tiers"])
 def test_tiny_graphs_match_bruteforce(ctxs, variant):
     for g in random_graphs(80, 11, 1):
         glob, pe = run_both(ctxs[variant], g)
@@ -73,7 +77,7 @@ def test_tiny_graphs_match_bruteforce(ctxs, variant):
         assert np.array_equal(pe, bf)
 
 
-@pytest.mark.parametrize("variant", VARIANTS + ["tiny_table"])
+@pytest.mark.parametrize("variant", VARIANTS + ["tiny_table", "all_tiers"])
 def test_structured_graphs_match_oracle(ctxs, variant):
     for g in structured_graphs():
         glob, pe = run_both(ctxs[variant], g)
@@ -81,10 +85,10 @@ def test_structured_graphs_match_oracle(ctxs, variant):
         assert np.array_equal(pe, oracle.o2_per_edge(g)), g.name
 
 
-@pytest.mark.parametrize("variant", VARIANTS + ["tiny_table"])
+@pytest.mark.parametrize("variant", VARIANTS + ["tiny_table", "all_tiers"])
 def test_medium_random_graphs(ctxs, variant):
     gs = [inputs.erdos_renyi(n, p, s) for s, (n, p) in enumerate([(257, 0.3), (1000, 0.02), (4099, 0.003)])]
-    gs += [inputs.chung_lu(20_000, 2.2, 90_000, 0.0, 3)]
+    gs += [inputs.chung_lu(20_000, 2.2, 90_000, 0.0, 3), inputs.chung_lu(200_000, 2.05, 900_000, 0.0, 6)]
     for g in gs:
         glob, pe = run_both(ctxs[variant], g)
         assert glob == oracle.o2_global(g), g.name
