@@ -166,6 +166,7 @@ int ensure_workspace(gd_graph *g, bool per_edge) {
         if ((rc = dalloc_n(g, &w.tcount, 64))) return rc;
         if ((rc = dalloc_n(g, &w.mlist, n))) return rc;
         if ((rc = dalloc_n(g, &w.west, n))) return rc;
+        if ((rc = dalloc_n(g, &w.tlist, n))) return rc;
     }
     if (!w.wtab && n > 0) {
         w.wtab_ctas = table_slots(g);
@@ -177,8 +178,9 @@ int ensure_workspace(gd_graph *g, bool per_edge) {
         if ((rc = dalloc_n(g, &w.tnode, n))) return rc;
         if ((rc = dalloc_n(g, &w.s1, n))) return rc;
         if ((rc = dalloc_n(g, &w.au, m))) return rc;
-        if ((rc = dalloc_n(g, &w.av, m))) return rc;
         if ((rc = dalloc_n(g, &w.dt, m))) return rc;
+        if ((rc = dalloc_n(g, &w.qcred, nnz))) return rc;
+        if ((rc = dalloc_n(g, &w.rcred, nnz))) return rc;
     }
     return GD_OK;
 }
@@ -446,25 +448,30 @@ static int count_path(gd_graph *g, bool per_edge, uint64_t *out_dev) {
         GD_CK(ctx, run_triangles_intersect(g));
         if (per_edge) GD_CK(ctx, run_per_edge_sums(g));
         GD_CK(ctx, run_literal(g));
-        GD_CK(ctx, run_final(g, variant, per_edge, false, out_dev));
+        GD_CK(ctx, run_final(g, variant, per_edge, false, false, out_dev));
         GD_CK(ctx, run_complete(g, 0));
         return GD_OK;
     }
     int32_t cnt[C_NUM];
     GD_CK(ctx, run_schedule(g, cnt));
-    bool cliq_credits = per_edge;
+    bool cliq_credits = per_edge, qr_credits = false;
     if (cnt[C_CL0 + 3] > 0) {
         // an out-degree above the bitmap kernels' limit: pairwise clique tests
         if ((rc = ensure_tribuf(g, variant))) return rc;
         GD_CK(ctx, run_triangles_intersect(g));
         GD_CK(ctx, run_cliques_pairwise(g));
         cliq_credits = true;
+        if (per_edge) GD_CK(ctx, run_per_edge_sums(g));
     } else {
         GD_CK(ctx, run_triangles_cliques(g, per_edge, cnt));
+        if (per_edge) {
+            GD_CK(ctx, run_node_sums(g));
+            GD_CK(ctx, run_triangle_sums(g, cnt));
+            qr_credits = true;
+        }
     }
-    if (per_edge) GD_CK(ctx, run_per_edge_sums(g));
     GD_CK(ctx, run_cycles(g, per_edge, cnt));
-    GD_CK(ctx, run_final(g, variant, per_edge, cliq_credits, out_dev));
+    GD_CK(ctx, run_final(g, variant, per_edge, cliq_credits, qr_credits, out_dev));
     GD_CK(ctx, run_complete(g, per_edge ? 0 : 1));
     return GD_OK;
 }

@@ -33,23 +33,28 @@ using namespace gdi::dev;
 // ---------------------------------------------------------------------------
 // CSR validation: sorted rows, ids in range, no self-loops, symmetric.
 // ---------------------------------------------------------------------------
+// One warp per row (hub rows have tens of thousands of entries).
 __global__ void k_validate(int32_t n, int64_t nnz, const int32_t *__restrict__ rp,
                            const int32_t *__restrict__ ci, int32_t *status) {
-    for (int32_t u = blockIdx.x * blockDim.x + threadIdx.x; u < n; u += gridDim.x * blockDim.x) {
+    const int lane = lane_id();
+    for (int32_t u = global_warp(); u < n; u += num_warps()) {
         const int32_t b = rp[u], e = rp[u + 1];
         // row bounds first: nothing is read through an unchecked bound
-        if (b < 0 || e < b || (int64_t)e > nnz) { atomicOr(status, ERR_CSR); atomicMin(status + 1, u); continue; }
-        for (int32_t p = b; p < e; p++) {
-            const int32_t v = ci[p];
-            bool bad = (v < 0 || v >= n || v == u || (p > b && v <= ci[p - 1]));
-            if (!bad) {
-                const int32_t vb = rp[v], ve = rp[v + 1];
-                bad = vb < 0 || ve < vb || (int64_t)ve > nnz;
-                // symmetric: u must appear in N(v)
-                if (!bad) bad = find_in(ci + vb, ve - vb, u) < 0;
+        bool bad = b < 0 || e < b || (int64_t)e > nnz;
+        if (!bad) {
+            for (int32_t p = b + lane; p < e; p += WARP) {
+                const int32_t v = ci[p];
+                bool pb = (v < 0 || v >= n || v == u || (p > b && v <= ci[p - 1]));
+                if (!pb) {
+                    const int32_t vb = rp[v], ve = rp[v + 1];
+                    pb = vb < 0 || ve < vb || (int64_t)ve > nnz;
+                    // symmetric: u must appear in N(v)
+                    if (!pb) pb = find_in(ci + vb, ve - vb, u) < 0;
+                }
+                bad |= pb;
             }
-            if (bad) { atomicOr(status, ERR_CSR); atomicMin(status + 1, u); break; }
         }
+        if (__any_sync(0xffffffffu, bad) && lane == 0) { atomicOr(status, ERR_CSR); atomicMin(status + 1, u); }
     }
 }
 
@@ -195,11 +200,11 @@ __global__ void k_node(int32_t n, const int32_t *__restrict__ rp, const int32_t 
     }
 }
 
-// Per edge: A_u = sum_{w in Tri} T(u,w), A_v = sum_{w in Tri} T(v,w),
-// D_T = sum_{w in Tri} d_w.
+// Per edge: A_u + A_v = sum_{w in Tri} (T(u,w) + T(v,w)) and
+// D_T = sum_{w in Tri} d_w (the per-edge identities need only the sum).
 __global__ void k_tri_sums(int64_t m, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
                            const int32_t *__restrict__ eu, const int32_t *__restrict__ ev,
-                           const uint32_t *__restrict__ tslot, uint64_t *au, uint64_t *av, uint64_t *dt) {
+                           const uint32_t *__restrict__ tslot, uint64_t *au, uint64_t *dt) {
     const int lane = lane_id();
     for (int64_t k = global_warp(); k < m; k += num_warps()) {
         int32_t u = eu[k], v = ev[k];
@@ -218,8 +223,7 @@ __global__ void k_tri_sums(int64_t m, const int32_t *__restrict__ rp, const int3
         }
         a_s = warp_sum(a_s); a_l = warp_sum(a_l); d = warp_sum(d);
         if (lane == 0) {
-            au[k] = su ? a_s : a_l;
-            av[k] = su ? a_l : a_s;
+            au[k] = a_s + a_l;      // A_u + A_v
             dt[k] = d;
         }
     }
@@ -379,7 +383,9 @@ struct FinalArgs {
     int cliq_credits;         // cliq_e from the per-slot credits (else summed by the clique kernel)
     const int32_t *rp, *eu, *ev, *eslot, *mate;
     const uint32_t *tslot;
-    const uint64_t *tnode, *s1, *au, *av, *dt;
+    const uint64_t *tnode, *s1, *au, *dt;        // au: A_u + A_v per edge
+    const unsigned long long *qcred, *rcred;     // triangle-perimeter / degree-sum credits per slot
+    int qr_credits;                              // A_u + A_v and D_T from the credits
     const unsigned long long *cacc, *yacc;
     uint64_t *out;
     unsigned long long *sums;
@@ -427,21 +433,29 @@ __global__ void k_final(FinalArgs a) {
             const int32_t q = a.mate[p];
             c4 = (int64_t)(a.yacc[p] + a.yacc[q]);
         }
-        const int64_t tsu = (int64_t)a.au[k] - T - 2 * cliq;
-        const int64_t tsv = (int64_t)a.av[k] - T - 2 * cliq;
-        const int64_t ts = tsu + tsv;
+        // A = A_u + A_v and D_T, then the restricted counts summed over both
+        // endpoints (the columns need only these sums):
+        //   N_TS1 = A - 2T - 4cliq, N_SS1 = t(u)+t(v) - 2T - 2cliq - N_TS1,
+        //   N_TI1 = D_T - 2T - 2cliq - N_TS1, cyc = C4(e) - N_TS1 - 2cliq,
+        //   N_SI1 = S1(u)+S1(v) - du - dv - 2D_T - Su - Sv - N_TS1 - 2N_SS1 - 2cyc
+        int64_t A, DT;
+        if (a.qr_credits) {
+            const int32_t q = a.mate[p];
+            A = (int64_t)(a.qcred[p] + a.qcred[q]) - T * T;
+            DT = (int64_t)(a.rcred[p] + a.rcred[q]) - T * (du + dv);
+        } else {
+            A = (int64_t)a.au[k];
+            DT = (int64_t)a.dt[k];
+        }
+        const int64_t ts = A - 2 * T - 4 * cliq;
         if (a.variant != GD_VARIANT_LITERAL) cyc = c4 - ts - 2 * cliq;
         loc[S_CYC] += cyc;
-        const int64_t susu = (int64_t)a.tnode[u] - T - cliq - tsu;
-        const int64_t svsv = (int64_t)a.tnode[v] - T - cliq - tsv;
-        const int64_t DT = (int64_t)a.dt[k];
+        const int64_t ss = (int64_t)a.tnode[u] + (int64_t)a.tnode[v] - 2 * T - 2 * cliq - ts;
         const int64_t ti = DT - 2 * T - 2 * cliq - ts;
-        const int64_t sui = ((int64_t)a.s1[u] - dv - DT - Su) - tsu - 2 * susu - cyc;
-        const int64_t svi = ((int64_t)a.s1[v] - du - DT - Sv) - tsv - 2 * svsv - cyc;
-        const int64_t ii1 = II - (cliq + ts + ti + susu + svsv + cyc + sui + svi);
-        if ((Su | Sv | I | tsu | tsv | susu | svsv | ti | cyc | sui | svi | ii1 | cliq) < 0) bad = 1;
+        const int64_t si = ((int64_t)a.s1[u] + (int64_t)a.s1[v] - du - dv - 2 * DT - Su - Sv) - ts - 2 * ss - 2 * cyc;
+        const int64_t ii1 = II - (cliq + ts + ti + ss + cyc + si);
+        if ((Su | Sv | I | A | DT | ts | ss | ti | cyc | si | ii1 | cliq) < 0) bad = 1;
         if (a.per_edge) {
-            const int64_t ss = susu + svsv, si = sui + svi;
             uint64_t *o = a.out + k * 15;
             o[0] = T;
             o[1] = Su + Sv;
@@ -576,7 +590,7 @@ cudaError_t validate_csr(gd_graph *g, int32_t *bad_index, int32_t *bad_code) {
     int32_t init[4] = {0, 0x7fffffff, 0, 0};
     cudaError_t e = cudaMemcpyAsync(w.status, init, sizeof(init), cudaMemcpyHostToDevice, st);
     if (e) return e;
-    if (g->n > 0) GD_LAUNCH(g, "k_validate", k_validate, grid_for(g->n, 256, sm_count(g) * 8), 256, 0, g->n, g->nnz, g->rp, g->ci, w.status);
+    if (g->n > 0) GD_LAUNCH(g, "k_validate", k_validate, grid_for((int64_t)g->n * 32, 256, sm_count(g) * 16), 256, 0, g->n, g->nnz, g->rp, g->ci, w.status);
     int32_t h[4];
     e = cudaMemcpyAsync(h, w.status, sizeof(h), cudaMemcpyDeviceToHost, st);
     if (e) return e;
@@ -623,15 +637,22 @@ cudaError_t run_triangles_intersect(gd_graph *g) {
     return cudaGetLastError();
 }
 
-cudaError_t run_per_edge_sums(gd_graph *g) {
+cudaError_t run_node_sums(gd_graph *g) {
     Workspace &w = g->ws;
-    cudaStream_t st = g->stream;
     const int sms = sm_count(g);
     if (g->n > 0)
         GD_LAUNCH(g, "k_node", k_node, grid_for((int64_t)g->n * 32, 256, sms * 16), 256, 0, g->n, g->rp, g->ci, w.tslot, w.tnode, w.s1);
+    return cudaGetLastError();
+}
+
+cudaError_t run_per_edge_sums(gd_graph *g) {
+    Workspace &w = g->ws;
+    const int sms = sm_count(g);
+    cudaError_t e = run_node_sums(g);
+    if (e) return e;
     if (g->m > 0)
         GD_LAUNCH(g, "k_tri_sums", k_tri_sums, grid_for(g->m * 32, 256, sms * 16), 256, 0, g->m, g->rp, g->ci, w.eu, w.ev, w.tslot,
-                                                                       w.au, w.av, w.dt);
+                                                                       w.au, w.dt);
     return cudaGetLastError();
 }
 
@@ -671,7 +692,8 @@ cudaError_t run_cliques_pairwise(gd_graph *g) {
     return cudaGetLastError();
 }
 
-cudaError_t run_final(gd_graph *g, int variant, bool per_edge, bool cliq_credits, uint64_t *out_dev) {
+cudaError_t run_final(gd_graph *g, int variant, bool per_edge, bool cliq_credits, bool qr_credits,
+                      uint64_t *out_dev) {
     Workspace &w = g->ws;
     const int sms = sm_count(g);
     if (g->m == 0) return cudaSuccess;
@@ -680,7 +702,9 @@ cudaError_t run_final(gd_graph *g, int variant, bool per_edge, bool cliq_credits
     a.need_restricted = per_edge ? 1 : 0;
     a.cliq_credits = cliq_credits ? 1 : 0;
     a.rp = g->rp; a.eu = w.eu; a.ev = w.ev; a.eslot = w.eslot; a.mate = w.mate; a.tslot = w.tslot;
-    a.tnode = w.tnode; a.s1 = w.s1; a.au = w.au; a.av = w.av; a.dt = w.dt;
+    a.tnode = w.tnode; a.s1 = w.s1; a.au = w.au; a.dt = w.dt;
+    a.qcred = (const unsigned long long *)w.qcred; a.rcred = (const unsigned long long *)w.rcred;
+    a.qr_credits = qr_credits ? 1 : 0;
     a.cacc = (const unsigned long long *)w.cacc; a.yacc = (const unsigned long long *)w.yacc;
     a.out = out_dev; a.sums = w.sums; a.status = w.status;
     GD_LAUNCH(g, "k_final", k_final, grid_for(g->m, 256, sms * 8), 256, 0, a);

@@ -43,11 +43,13 @@ enum CounterIdx {
     C_HUB = 3,      // hubs (whole-GPU batches)
     C_CL0 = 4,      // 4 clique buckets by out-degree: <=CL_D0, <=CL_D1, <=CL_D2, larger
     C_DYN = 8,      // dynamic work index of the medium tier
+    C_TINY = 9,     // vertices in the warp-level wedge tier
     C_MB0 = 16,     // medium tier: vertices per log2(wedges) bucket (40 buckets)
     C_MOFF = 64,    // medium tier: placement offsets per bucket (40)
     C_NUM = 112
 };
 constexpr int MB_BUCKETS = 40;
+constexpr int TINY_WEDGES = 256;   // warp-level wedge table of 2 * TINY_WEDGES entries
 constexpr int CL_D0 = 64, CL_D1 = 256, CL_D2 = 1024;
 constexpr long long HUB_MIN_WEDGES = 1ll << 18;
 
@@ -71,7 +73,8 @@ struct Workspace {
     // per-edge mode
     uint64_t *tnode = nullptr;     // [n] edges inside N(x)
     uint64_t *s1 = nullptr;        // [n] sum of neighbour degrees
-    uint64_t *au = nullptr, *av = nullptr, *dt = nullptr;   // [m]
+    uint64_t *au = nullptr, *dt = nullptr;   // [m] A_u + A_v and D_T (intersection path)
+    uint64_t *qcred = nullptr, *rcred = nullptr;   // [nnz] triangle perimeter / degree-sum credits
     uint64_t *cacc = nullptr;      // [nnz] 4-clique credits per slot
     uint64_t *yacc = nullptr;      // [nnz] 4-cycle credits per slot (or cyc_e for literal)
     // schedule
@@ -85,6 +88,7 @@ struct Workspace {
     uint32_t *tcred = nullptr;     // [nnz] triangle credits per slot
     int32_t *touched = nullptr;    // [table slots * n] touched entries of the dense wedge tables
     int32_t *mlist = nullptr;      // [n] medium tier sorted by decreasing wedge work
+    int32_t *tlist = nullptr;      // [n] tiny tier (warp per vertex)
     int64_t *west = nullptr;       // [n] wedge work of medium vertices
     int32_t *tcount = nullptr;     // [64]
     // scratch
@@ -166,10 +170,13 @@ cudaError_t run_triangles_intersect(gd_graph *g);         // |Tri| per slot by i
 cudaError_t run_per_edge_sums(gd_graph *g);               // t(x), S1(x), A_u, A_v, D_T
 cudaError_t run_literal(gd_graph *g);                     // Algorithm 2 CliqueCount / CycleCount
 cudaError_t run_cliques_pairwise(gd_graph *g);            // 4-clique credits, any out-degree
-cudaError_t run_final(gd_graph *g, int variant, bool per_edge, bool cliq_credits, uint64_t *out_dev);
+cudaError_t run_final(gd_graph *g, int variant, bool per_edge, bool cliq_credits, bool qr_credits,
+                      uint64_t *out_dev);
 // gd_step2.cu
 cudaError_t run_schedule(gd_graph *g, int32_t *counters_host);
 cudaError_t run_triangles_cliques(gd_graph *g, bool per_edge, const int32_t *counters_host);
+cudaError_t run_triangle_sums(gd_graph *g, const int32_t *counters_host);   // Q/R credits (needs |Tri|)
+cudaError_t run_node_sums(gd_graph *g);                                      // t(x), S1(x)
 cudaError_t run_cycles(gd_graph *g, bool per_edge, const int32_t *counters_host);
 int32_t table_slots(gd_graph *g);
 cudaError_t run_complete(gd_graph *g, int derive_cyc);

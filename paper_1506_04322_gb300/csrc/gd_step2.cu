@@ -67,7 +67,7 @@ __global__ void k_neighbor_degree(int64_t nnz, const int32_t *__restrict__ rp, c
 __global__ void k_schedule(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
                            const int32_t *__restrict__ nd, int64_t small_cap, int64_t hub_min, int32_t cl_max,
                            int32_t *vlist, int32_t *hubs, int32_t *clist, int32_t *counters, int64_t *dplus,
-                           int64_t *west) {
+                           int64_t *west, int32_t *tlist) {
     const int lane = lane_id();
     for (int32_t u = global_warp(); u < n; u += num_warps()) {
         const int32_t bu = rp[u], du = rp[u + 1] - bu;
@@ -83,7 +83,8 @@ __global__ void k_schedule(int32_t n, const int32_t *__restrict__ rp, const int3
             dplus[u] = dp;
             atomicMax(counters + C_MAXDP, dp);
             if (est > 0) {
-                if (est <= small_cap) vlist[atomicAdd(counters + C_SMALL, 1)] = u;
+                if (est <= TINY_WEDGES) tlist[atomicAdd(counters + C_TINY, 1)] = u;
+                else if (est <= small_cap) vlist[atomicAdd(counters + C_SMALL, 1)] = u;
                 else if (est <= hub_min) {
                     vlist[n - 1 - atomicAdd(counters + C_MEDIUM, 1)] = u;
                     west[u] = est;
@@ -155,9 +156,13 @@ struct CliqueArgs {
     const int32_t *counters;
     int bucket;
     int32_t n;
+    const int32_t *rp;
     const int32_t *dag_off, *dag_col, *dag_slot, *dag_nd;
     unsigned long long *cacc;   // per-slot clique credits (per-edge mode)
     uint32_t *tcred;            // per-slot triangle credits
+    const uint32_t *tslot;      // |Tri| per slot (triangle-sum mode)
+    unsigned long long *qcred;  // per-slot triangle-perimeter credits (triangle-sum mode)
+    unsigned long long *rcred;  // per-slot triangle degree-sum credits (triangle-sum mode)
     unsigned long long *sums;   // u128 sums (S_CLIQ gets 6 * K4 in global mode)
     int32_t *status;            // error bits
 };
@@ -170,10 +175,29 @@ struct CliqueSmem {
     int32_t rank_of[DMAX];      // rank index of ids[k] within N+(a)
     int32_t rid[DMAX], rslot[DMAX], rdeg[DMAX];   // by rank index
     uint32_t cnt_p[DMAX], tri_p[DMAX];
+    unsigned long long qa[DMAX], ra[DMAX];         // triangle-sum mode
     uint32_t M[DMAX * W];       // adjacency, row r = node of rank index r
 };
 
-template <int DMAX, int THREADS, bool CREDIT>
+// MODE_COUNT: |Tri| credits + number of 4-cliques (global counts)
+// MODE_CREDIT: |Tri| credits + 4-clique credits on all six edges (per edge)
+// MODE_TRISUM: per triangle {a,b,c} with T the final |Tri| of its edges,
+//   perimeter P = T(a,b)+T(a,c)+T(b,c) and degree sum d_a+d_b+d_c credited
+//   to each of its three edges; per edge e the credits add up to
+//   Q(e) = A_u + A_v + T(e)^2 and R(e) = D_T + T(e)(d_u + d_v).
+enum { MODE_COUNT = 0, MODE_CREDIT = 1, MODE_TRISUM = 2 };
+
+// binary search of id `key` in the out-list of node x; returns the CSR slot
+// of the edge (x, key) or -1
+__device__ __forceinline__ int32_t out_slot(const CliqueArgs &a, int32_t x, int32_t key) {
+    const int32_t o = a.dag_off[x], d = a.dag_off[x + 1] - o;
+    int32_t lo = 0, hi = d;
+    while (lo < hi) { const int32_t mid = (lo + hi) >> 1; if (ldg(a.dag_col + o + mid) < key) lo = mid + 1; else hi = mid; }
+    if (lo >= d || ldg(a.dag_col + o + lo) != key) return -1;
+    return ldg(a.dag_slot + o + lo);
+}
+
+template <int DMAX, int THREADS, int MODE>
 __global__ void __launch_bounds__(THREADS)
 k_clique_bitmap(CliqueArgs a) {
     constexpr int W = DMAX / 32;
@@ -193,7 +217,10 @@ k_clique_bitmap(CliqueArgs a) {
         const int Wd = (D + 31) >> 5;
         for (int k = threadIdx.x; k < D; k += THREADS) { S.ids[k] = a.dag_col[off + k]; S.degs[k] = a.dag_nd[off + k]; }
         for (int k = threadIdx.x; k < D * Wd; k += THREADS) S.M[k] = 0;
-        for (int k = threadIdx.x; k < D; k += THREADS) { S.cnt_p[k] = 0; S.tri_p[k] = 0; }
+        for (int k = threadIdx.x; k < D; k += THREADS) {
+            if (MODE == MODE_TRISUM) { S.qa[k] = 0; S.ra[k] = 0; }
+            else { S.cnt_p[k] = 0; S.tri_p[k] = 0; }
+        }
         __syncthreads();
         // rank index of each out-neighbour (number of out-neighbours below it)
         for (int k = threadIdx.x; k < D; k += THREADS) {
@@ -220,6 +247,7 @@ k_clique_bitmap(CliqueArgs a) {
             }
         }
         __syncthreads();
+        const int32_t da = a.rp[va + 1] - a.rp[va];
         // for each b (rank index rb): S_b = M[rb] & ranks above rb
         for (int rb = warp; rb < D; rb += NW) {
             uint32_t nS = 0;
@@ -235,7 +263,31 @@ k_clique_bitmap(CliqueArgs a) {
             __syncwarp();
             if (nS == 0) continue;
             const int32_t b = S.rid[rb];
-            const int32_t bo = a.dag_off[b], bd = a.dag_off[b + 1] - bo;
+            if (MODE == MODE_TRISUM) {
+                const unsigned long long tab = a.tslot[S.rslot[rb]];
+                const unsigned long long dsum_ab = (unsigned long long)da + S.rdeg[rb];
+                unsigned long long qsum = 0, rsum = 0;
+                for (int q = rb + 1 + lane; q < D; q += WARP) {
+                    if (!((mys[q >> 5] >> (q & 31)) & 1u)) continue;
+                    const int32_t sbc = out_slot(a, b, S.rid[q]);
+                    if (sbc < 0) { atomicOr(a.status, ERR_CAPACITY); continue; }
+                    const unsigned long long P = tab + a.tslot[S.rslot[q]] + a.tslot[sbc];
+                    const unsigned long long R = dsum_ab + S.rdeg[q];
+                    qsum += P; rsum += R;
+                    atomicAdd(&S.qa[q], P);
+                    atomicAdd(&S.ra[q], R);
+                    atomicAdd(a.qcred + sbc, P);
+                    atomicAdd(a.rcred + sbc, R);
+                }
+                qsum = warp_sum(qsum);
+                rsum = warp_sum(rsum);
+                if (lane == 0) {
+                    atomicAdd(a.qcred + S.rslot[rb], qsum);
+                    atomicAdd(a.rcred + S.rslot[rb], rsum);
+                }
+                __syncwarp();
+                continue;
+            }
             unsigned long long k2 = 0;   // ordered adjacent pairs inside S_b
             for (int q = rb + 1 + lane; q < D; q += WARP) {
                 if (!((mys[q >> 5] >> (q & 31)) & 1u)) continue;
@@ -243,20 +295,17 @@ k_clique_bitmap(CliqueArgs a) {
                 for (int w = 0; w < Wd; w++) kq += __popc(S.M[q * Wd + w] & mys[w]);
                 k2 += kq;
                 atomicAdd(&S.tri_p[q], 1u);
-                if (CREDIT) atomicAdd(&S.cnt_p[q], kq);
+                if (MODE == MODE_CREDIT) atomicAdd(&S.cnt_p[q], kq);
                 // slot of (b, c_q): c_q is in N+(b)
-                const int32_t cq = S.rid[q];
-                int32_t lo = 0, hi = bd;
-                while (lo < hi) { const int32_t mid = (lo + hi) >> 1; if (ldg(a.dag_col + bo + mid) < cq) lo = mid + 1; else hi = mid; }
-                if (lo >= bd || ldg(a.dag_col + bo + lo) != cq) { atomicOr(a.status, ERR_CAPACITY); continue; }
-                const int32_t sbc = ldg(a.dag_slot + bo + lo);
+                const int32_t sbc = out_slot(a, b, S.rid[q]);
+                if (sbc < 0) { atomicOr(a.status, ERR_CAPACITY); continue; }
                 atomicAdd(a.tcred + sbc, 1u);
-                if (CREDIT && kq) atomicAdd(a.cacc + sbc, (unsigned long long)kq);
+                if (MODE == MODE_CREDIT && kq) atomicAdd(a.cacc + sbc, (unsigned long long)kq);
             }
             k2 = warp_sum(k2);
             if (lane == 0) {
                 atomicAdd(a.tcred + S.rslot[rb], nS);
-                if (CREDIT && k2) atomicAdd(a.cacc + S.rslot[rb], k2 >> 1);
+                if (MODE == MODE_CREDIT && k2) atomicAdd(a.cacc + S.rslot[rb], k2 >> 1);
                 k4_local += k2 >> 1;
             }
             __syncwarp();
@@ -264,13 +313,17 @@ k_clique_bitmap(CliqueArgs a) {
         __syncthreads();
         // per-node credits of (a, c) and pair credits of edges (c, d) inside N+(a)
         for (int q = threadIdx.x; q < D; q += THREADS) {
-            if (S.tri_p[q]) atomicAdd(a.tcred + S.rslot[q], S.tri_p[q]);
-            if (CREDIT && S.cnt_p[q]) atomicAdd(a.cacc + S.rslot[q], (unsigned long long)S.cnt_p[q]);
+            if (MODE == MODE_TRISUM) {
+                if (S.qa[q]) atomicAdd(a.qcred + S.rslot[q], S.qa[q]);
+                if (S.ra[q]) atomicAdd(a.rcred + S.rslot[q], S.ra[q]);
+            } else {
+                if (S.tri_p[q]) atomicAdd(a.tcred + S.rslot[q], S.tri_p[q]);
+                if (MODE == MODE_CREDIT && S.cnt_p[q]) atomicAdd(a.cacc + S.rslot[q], (unsigned long long)S.cnt_p[q]);
+            }
         }
-        if (CREDIT) {
+        if (MODE == MODE_CREDIT) {
             for (int p = warp; p < D; p += NW) {
                 const int32_t cp = S.rid[p];
-                const int32_t po = a.dag_off[cp], pd = a.dag_off[cp + 1] - po;
                 const int pw = p >> 5;
                 for (int q = p + 1 + lane; q < D; q += WARP) {
                     if (!((S.M[p * Wd + (q >> 5)] >> (q & 31)) & 1u)) continue;
@@ -279,17 +332,15 @@ k_clique_bitmap(CliqueArgs a) {
                     if (p & 31) pc += __popc(S.M[p * Wd + pw] & S.M[q * Wd + pw] & ((1u << (p & 31)) - 1u));
                     if (!pc) continue;
                     // c_p ranks below c_q, so c_q is in N+(c_p)
-                    const int32_t cq = S.rid[q];
-                    int32_t lo = 0, hi = pd;
-                    while (lo < hi) { const int32_t mid = (lo + hi) >> 1; if (ldg(a.dag_col + po + mid) < cq) lo = mid + 1; else hi = mid; }
-                    if (lo >= pd || ldg(a.dag_col + po + lo) != cq) { atomicOr(a.status, ERR_CAPACITY); continue; }
-                    atomicAdd(a.cacc + ldg(a.dag_slot + po + lo), (unsigned long long)pc);
+                    const int32_t scd = out_slot(a, cp, S.rid[q]);
+                    if (scd < 0) { atomicOr(a.status, ERR_CAPACITY); continue; }
+                    atomicAdd(a.cacc + scd, (unsigned long long)pc);
                 }
             }
         }
         __syncthreads();
     }
-    if (!CREDIT) {
+    if (MODE == MODE_COUNT) {
         __shared__ unsigned long long red[NW];
         const unsigned long long x = warp_sum(k4_local);
         if (lane == 0) red[warp] = x;
@@ -399,7 +450,7 @@ __device__ __forceinline__ uint32_t sm_find(const int32_t *keys, const uint32_t 
 struct CycleArgs {
     int32_t n;
     const int32_t *rp, *ci, *nd;
-    const int32_t *vlist, *hubs, *mlist;
+    const int32_t *vlist, *hubs, *mlist, *tlist;
     int32_t *counters;           // counters[C_DYN] is the medium tier's work index
     uint32_t capmask;
     uint32_t *tables;            // [slots][n] dense counters, zero at rest
@@ -411,6 +462,78 @@ struct CycleArgs {
 };
 
 __device__ __forceinline__ unsigned long long c2(uint32_t c) { return (unsigned long long)c * (c - 1) / 2; }
+
+// Tiny tier: one warp per vertex (at most TINY_WEDGES wedges), each warp
+// with its own shared-memory hash of 2 * TINY_WEDGES entries; no CTA barriers.
+template <bool CREDIT>
+__global__ void __launch_bounds__(256)
+k_cycles_tiny(CycleArgs a) {
+    constexpr int NW = 8, TCAP = 2 * TINY_WEDGES;
+    constexpr uint32_t TMASK = TCAP - 1;
+    __shared__ int32_t keys[NW][TCAP];
+    __shared__ uint32_t vals[NW][TCAP];
+    __shared__ int32_t touched[NW][TINY_WEDGES];
+    __shared__ int32_t ntch[NW];
+    __shared__ unsigned long long item[NW][WARP];
+    const int lane = lane_id(), warp = threadIdx.x >> 5;
+    int32_t *K = keys[warp];
+    uint32_t *V = vals[warp];
+    int32_t *tl = touched[warp];
+    for (int i = lane; i < TCAP; i += WARP) { K[i] = -1; V[i] = 0; }
+    if (lane == 0) ntch[warp] = 0;
+    item[warp][lane] = 0;
+    __syncwarp();
+    const int32_t nv = a.counters[C_TINY];
+    unsigned long long c4 = 0;
+    for (int32_t idx = global_warp(); idx < nv; idx += num_warps()) {
+        const int32_t u = a.tlist[idx];
+        const int32_t bu = a.rp[u], du = a.rp[u + 1] - bu;
+        warp_wedges(u, du, bu, 0, du, WARP, a.rp, a.ci, a.nd,
+            [&](int k, int32_t q, int32_t y, bool ok, bool live) {
+                if (!ok) return;
+                uint32_t h = hash32((uint32_t)y) & TMASK;
+                uint32_t old = 0;
+                while (true) {
+                    const int32_t kk = K[h];
+                    if (kk == y) { old = atomicAdd(V + h, 1u); break; }
+                    if (kk == -1) {
+                        const int32_t prev = atomicCAS(K + h, -1, y);
+                        if (prev == -1) { old = atomicAdd(V + h, 1u); tl[atomicAdd(&ntch[warp], 1)] = (int32_t)h; break; }
+                        if (prev == y) { old = atomicAdd(V + h, 1u); break; }
+                    }
+                    h = (h + 1) & TMASK;
+                }
+                if (!CREDIT) c4 += old;
+            },
+            [&](int32_t) {});
+        __syncwarp();
+        if (CREDIT) {
+            warp_wedges(u, du, bu, 0, du, WARP, a.rp, a.ci, a.nd,
+                [&](int k, int32_t q, int32_t y, bool ok, bool live) {
+                    const uint32_t c = ok ? sm_find(K, V, TMASK, y) : 0;
+                    if (c > 1) atomicAdd(a.yacc + q, (unsigned long long)(c - 1));
+                    item_add(item[warp], k, c > 1 ? c - 1 : 0, live);
+                },
+                [&](int32_t it) {
+                    __syncwarp();
+                    const unsigned long long s = item[warp][lane];
+                    if (s) { atomicAdd(a.yacc + bu + it + lane, s); item[warp][lane] = 0; }
+                    __syncwarp();
+                });
+            __syncwarp();
+        }
+        const int32_t nt = ntch[warp];
+        for (int32_t i = lane; i < nt; i += WARP) { const int32_t h = tl[i]; K[h] = -1; V[h] = 0; }
+        __syncwarp();
+        if (lane == 0) ntch[warp] = 0;
+        __syncwarp();
+    }
+    if (!CREDIT) {
+        c4 = warp_sum(c4);
+        if (lane == 0) add_u128(a.sums + 2 * (S_NUM + X_C4), 4 * c4);
+    }
+}
+
 
 template <int THREADS, bool CREDIT>
 __global__ void __launch_bounds__(THREADS)
@@ -670,7 +793,8 @@ cudaError_t run_schedule(gd_graph *g, int32_t *counters_host) {
         const int64_t small_cap = g->ctx->opt.smem_table_max / 2;
         GD_LAUNCH(g, "k_schedule", k_schedule, grid_for((int64_t)n * 32, 256, sms * 16), 256, 0,
                   n, g->rp, g->ci, w.nd, small_cap, (int64_t)1 << g->ctx->opt.hub_wedges_log2,
-                  g->ctx->opt.bitmap_max_outdeg, w.vlist, w.hubs, w.clist, w.counters, w.scan_tmp, w.west);
+                  g->ctx->opt.bitmap_max_outdeg, w.vlist, w.hubs, w.clist, w.counters, w.scan_tmp, w.west,
+                  w.tlist);
         GD_LAUNCH(g, "k_medium_offsets", k_medium_offsets, 1, 32, 0, w.counters);
         GD_LAUNCH(g, "k_medium_place", k_medium_place, grid_for(n, 256, sms * 4), 256, 0, n, w.vlist, w.west,
                   w.counters, w.mlist);
@@ -694,27 +818,38 @@ size_t clique_smem_bytes(int dmax, int threads) {
     return (size_t)dmax * 4 * 7 + (size_t)dmax * W * 4 + (size_t)(threads / 32) * W * 4 + 64;
 }
 
-template <int DMAX, int THREADS, bool CREDIT>
+template <int DMAX, int THREADS, int MODE>
 static cudaError_t launch_clique(gd_graph *g, int bucket, int count) {
     if (count == 0) return cudaSuccess;
     Workspace &w = g->ws;
     CliqueArgs a;
-    a.clist = w.clist; a.counters = w.counters; a.bucket = bucket; a.n = g->n;
+    a.clist = w.clist; a.counters = w.counters; a.bucket = bucket; a.n = g->n; a.rp = g->rp;
     a.dag_off = w.dag_off; a.dag_col = w.dag_col; a.dag_slot = w.dag_slot; a.dag_nd = w.dag_nd;
-    a.cacc = (unsigned long long *)w.cacc; a.tcred = w.tcred; a.sums = w.sums; a.status = w.status;
+    a.cacc = (unsigned long long *)w.cacc; a.tcred = w.tcred; a.tslot = w.tslot;
+    a.qcred = (unsigned long long *)w.qcred; a.rcred = (unsigned long long *)w.rcred;
+    a.sums = w.sums; a.status = w.status;
     const size_t smem = sizeof(CliqueSmem<DMAX>) + (size_t)(THREADS / 32) * (DMAX / 32) * 4;
-    cudaError_t e = allow_smem(k_clique_bitmap<DMAX, THREADS, CREDIT>, smem);
+    cudaError_t e = allow_smem(k_clique_bitmap<DMAX, THREADS, MODE>, smem);
     if (e) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_clique_bitmap<DMAX, THREADS, CREDIT>, THREADS, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_clique_bitmap<DMAX, THREADS, MODE>, THREADS, smem);
     if (e) return e;
     const unsigned grid = grid_for(count, 1, sms_of(g) * (per_sm > 0 ? per_sm : 1));
-    GD_LAUNCH(g, "k_clique_bitmap", (k_clique_bitmap<DMAX, THREADS, CREDIT>), grid, THREADS, smem, a);
+    const char *name = MODE == MODE_TRISUM ? "k_trisum_bitmap" : "k_clique_bitmap";
+    GD_LAUNCH(g, name, (k_clique_bitmap<DMAX, THREADS, MODE>), grid, THREADS, smem, a);
     return cudaGetLastError();
 }
 
+template <int MODE>
+static cudaError_t launch_clique_buckets(gd_graph *g, const int32_t *cnt) {
+    cudaError_t e;
+    if ((e = launch_clique<CL_D0, 32, MODE>(g, 0, cnt[C_CL0]))) return e;
+    if ((e = launch_clique<CL_D1, 128, MODE>(g, 1, cnt[C_CL0 + 1]))) return e;
+    return launch_clique<CL_D2, 512, MODE>(g, 2, cnt[C_CL0 + 2]);
+}
+
 // Triangles per slot and 4-cliques (credits when per_edge).  Requires the
-// largest out-degree <= CL_D2 (checked by the caller).
+// largest out-degree <= bitmap limit (checked by the caller).
 cudaError_t run_triangles_cliques(gd_graph *g, bool per_edge, const int32_t *cnt) {
     Workspace &w = g->ws;
     const int sms = sms_of(g);
@@ -724,17 +859,24 @@ cudaError_t run_triangles_cliques(gd_graph *g, bool per_edge, const int32_t *cnt
     if (per_edge) {
         e = cudaMemsetAsync(w.cacc, 0, sizeof(uint64_t) * g->nnz, g->stream);
         if (e) return e;
-        if ((e = launch_clique<CL_D0, 32, true>(g, 0, cnt[C_CL0]))) return e;
-        if ((e = launch_clique<CL_D1, 128, true>(g, 1, cnt[C_CL0 + 1]))) return e;
-        if ((e = launch_clique<CL_D2, 512, true>(g, 2, cnt[C_CL0 + 2]))) return e;
+        if ((e = launch_clique_buckets<MODE_CREDIT>(g, cnt))) return e;
     } else {
-        if ((e = launch_clique<CL_D0, 32, false>(g, 0, cnt[C_CL0]))) return e;
-        if ((e = launch_clique<CL_D1, 128, false>(g, 1, cnt[C_CL0 + 1]))) return e;
-        if ((e = launch_clique<CL_D2, 512, false>(g, 2, cnt[C_CL0 + 2]))) return e;
+        if ((e = launch_clique_buckets<MODE_COUNT>(g, cnt))) return e;
     }
     GD_LAUNCH(g, "k_tri_symmetrize", k_tri_symmetrize, grid_for(g->m, 256, sms * 8), 256, 0,
               g->m, w.eslot, w.mate, w.tcred, w.tslot);
     return cudaGetLastError();
+}
+
+// Per-edge A_u + A_v and D_T through triangle credits (needs final |Tri|).
+cudaError_t run_triangle_sums(gd_graph *g, const int32_t *cnt) {
+    Workspace &w = g->ws;
+    if (g->m == 0) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(w.qcred, 0, sizeof(uint64_t) * g->nnz, g->stream);
+    if (e) return e;
+    e = cudaMemsetAsync(w.rcred, 0, sizeof(uint64_t) * g->nnz, g->stream);
+    if (e) return e;
+    return launch_clique_buckets<MODE_TRISUM>(g, cnt);
 }
 
 int32_t hub_batch(gd_graph *g) {
@@ -764,7 +906,7 @@ cudaError_t run_cycles(gd_graph *g, bool per_edge, const int32_t *cnt) {
     }
     CycleArgs a;
     a.n = g->n; a.rp = g->rp; a.ci = g->ci; a.nd = w.nd;
-    a.vlist = w.vlist; a.hubs = w.hubs; a.mlist = w.mlist; a.counters = w.counters;
+    a.vlist = w.vlist; a.hubs = w.hubs; a.mlist = w.mlist; a.tlist = w.tlist; a.counters = w.counters;
     a.capmask = (uint32_t)(g->ctx->opt.smem_table_max - 1);
     a.tables = w.wtab; a.touched = w.touched; a.tcount = w.tcount;
     a.yacc = (unsigned long long *)w.yacc; a.sums = w.sums;
@@ -785,6 +927,11 @@ cudaError_t run_cycles(gd_graph *g, bool per_edge, const int32_t *cnt) {
         const unsigned grid = (unsigned)(cnt[C_MEDIUM] < slots ? cnt[C_MEDIUM] : slots);
         if (per_edge) GD_LAUNCH(g, "k_cycles_medium", (k_cycles_medium<1024, true>), grid, 1024, 0, a);
         else GD_LAUNCH(g, "k_cycles_medium", (k_cycles_medium<1024, false>), grid, 1024, 0, a);
+    }
+    // tiny tier
+    if (cnt[C_TINY] > 0) {
+        if (per_edge) GD_LAUNCH(g, "k_cycles_tiny", k_cycles_tiny<true>, grid_for((int64_t)cnt[C_TINY] * 32, 256, sms * 5), 256, 0, a);
+        else GD_LAUNCH(g, "k_cycles_tiny", k_cycles_tiny<false>, grid_for((int64_t)cnt[C_TINY] * 32, 256, sms * 5), 256, 0, a);
     }
     // small tier
     if (cnt[C_SMALL] > 0) {
