@@ -510,11 +510,141 @@ int gd_count_per_edge(gd_graph *g, uint64_t *out, int out_flags, gd_u128 global_
     return read_results(g, global_out);
 }
 
+// Scoped device blocks from the context pool (released on scope exit).
+struct PoolBlocks {
+    gd_ctx *ctx;
+    std::vector<std::pair<void *, size_t>> bl;
+    explicit PoolBlocks(gd_ctx *c) : ctx(c) {}
+    int get(void **p, size_t bytes) {
+        int rc = ctx_alloc(ctx, p, bytes);
+        if (rc == GD_OK) bl.emplace_back(*p, bytes);
+        return rc;
+    }
+    ~PoolBlocks() { for (auto &b : bl) ctx_release(ctx, b.first, b.second); }
+};
+
 int gd_count_batch(gd_ctx *ctx, int32_t num_graphs, const int32_t *graph_node_ptr, const int32_t *row_ptr,
                    const int32_t *col_idx, int flags, uint64_t *out) {
     if (!ctx) return GD_EINVAL;
-    (void)num_graphs; (void)graph_node_ptr; (void)row_ptr; (void)col_idx; (void)flags; (void)out;
-    return fail(ctx, GD_ENOTIMPL, "gd_count_batch: not built yet");
+    ctx->err.clear();
+    if (num_graphs < 0 || !graph_node_ptr || !row_ptr || !out)
+        return fail(ctx, GD_EINVAL, "gd_count_batch: null pointer or negative graph count");
+    GD_CK(ctx, cudaSetDevice(ctx->device));
+    if (num_graphs == 0) return GD_OK;
+    const bool dev = (flags & GD_DEVICE_PTRS) != 0;
+    const bool dev_out = (flags & GD_OUT_DEVICE) != 0;
+    cudaStream_t st = ctx->stream;
+    // graph offsets on the host (they decide the kernel variant and the fallback)
+    std::vector<int32_t> gnp((size_t)num_graphs + 1);
+    if (dev) {
+        GD_CK(ctx, cudaMemcpyAsync(gnp.data(), graph_node_ptr, sizeof(int32_t) * gnp.size(), cudaMemcpyDeviceToHost, st));
+        GD_CK(ctx, cudaStreamSynchronize(st));
+    } else {
+        memcpy(gnp.data(), graph_node_ptr, sizeof(int32_t) * gnp.size());
+    }
+    if (gnp[0] != 0) return fail(ctx, GD_EINVAL, "graph_node_ptr[0] must be 0");
+    int32_t nmax_graph = 0;
+    for (int32_t i = 0; i < num_graphs; i++) {
+        if (gnp[i + 1] < gnp[i]) return fail(ctx, GD_EINVAL, "graph_node_ptr decreases at graph %d", i);
+        nmax_graph = std::max(nmax_graph, gnp[i + 1] - gnp[i]);
+    }
+    if (nmax_graph > 65535)
+        return fail(ctx, GD_EOVERFLOW, "a graph of the batch has %d nodes; per-graph uint64 counts need <= 65535",
+                    nmax_graph);
+    const int32_t N = gnp[num_graphs];
+    int32_t nnz32 = 0;
+    if (dev) {
+        GD_CK(ctx, cudaMemcpyAsync(&nnz32, row_ptr + N, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        GD_CK(ctx, cudaStreamSynchronize(st));
+    } else {
+        nnz32 = row_ptr[N];
+        if (row_ptr[0] != 0) return fail(ctx, GD_EINVAL, "row_ptr[0] must be 0");
+        for (int32_t u = 0; u < N; u++)
+            if (row_ptr[u + 1] < row_ptr[u]) return fail(ctx, GD_EINVAL, "row_ptr decreases at row %d", u);
+    }
+    const int64_t nnz = nnz32;
+    if (nnz < 0 || (nnz & 1)) return fail(ctx, GD_EINVAL, "row_ptr[N] must be a non-negative even count");
+    if (nnz > 0 && !col_idx) return fail(ctx, GD_EINVAL, "null col_idx");
+    PoolBlocks pb(ctx);
+    int rc;
+    const int32_t *d_gnp = graph_node_ptr, *d_rp = row_ptr, *d_ci = col_idx;
+    if (!dev) {
+        int32_t *a, *b, *c;
+        if ((rc = pb.get((void **)&a, sizeof(int32_t) * gnp.size()))) return rc;
+        if ((rc = pb.get((void **)&b, sizeof(int32_t) * ((size_t)N + 1)))) return rc;
+        if ((rc = pb.get((void **)&c, sizeof(int32_t) * (size_t)std::max<int64_t>(nnz, 1)))) return rc;
+        GD_CK(ctx, cudaMemcpyAsync(a, gnp.data(), sizeof(int32_t) * gnp.size(), cudaMemcpyHostToDevice, st));
+        GD_CK(ctx, cudaMemcpyAsync(b, row_ptr, sizeof(int32_t) * ((size_t)N + 1), cudaMemcpyHostToDevice, st));
+        if (nnz > 0) GD_CK(ctx, cudaMemcpyAsync(c, col_idx, sizeof(int32_t) * (size_t)nnz, cudaMemcpyHostToDevice, st));
+        d_gnp = a; d_rp = b; d_ci = c;
+    }
+    unsigned long long *d_out = (unsigned long long *)out;
+    if (!dev_out) {
+        if ((rc = pb.get((void **)&d_out, sizeof(uint64_t) * 15 * (size_t)num_graphs))) return rc;
+    }
+    int32_t *d_misc;    // [0] work index, [1] status, [2] big count, [3..6] validate status
+    int32_t *d_big;
+    if ((rc = pb.get((void **)&d_misc, 64 * sizeof(int32_t)))) return rc;
+    if ((rc = pb.get((void **)&d_big, sizeof(int32_t) * (size_t)num_graphs))) return rc;
+    // validate the packed union (rows sorted, ids in range, no self-loops, symmetric)
+    {
+        gd_graph tmp;
+        tmp.ctx = ctx; tmp.stream = st; tmp.n = N; tmp.nnz = nnz; tmp.m = nnz / 2;
+        tmp.rp = const_cast<int32_t *>(d_rp); tmp.ci = const_cast<int32_t *>(d_ci);
+        tmp.ws.status = d_misc + 8;
+        int32_t bad_index = -1, bad_code = 0;
+        GD_CK(ctx, validate_csr(&tmp, &bad_index, &bad_code));
+        tmp.ws = Workspace();
+        if (bad_code)
+            return fail(ctx, GD_EINVAL, "invalid batch CSR at row %d: rows must be strictly ascending, ids in range, "
+                        "no self-loops, every edge stored in both directions", bad_index);
+    }
+    GD_CK(ctx, cudaMemsetAsync(d_misc, 0, 8 * sizeof(int32_t), st));
+    const int nmax = nmax_graph <= 512 ? 512 : 1024;
+    GD_CK(ctx, launch_batch_count(ctx, st, num_graphs, d_gnp, d_rp, d_ci, d_misc, d_out, d_misc + 1, d_big,
+                                  d_misc + 2, nmax));
+    int32_t misc[3];
+    GD_CK(ctx, cudaMemcpyAsync(misc, d_misc, sizeof(misc), cudaMemcpyDeviceToHost, st));
+    GD_CK(ctx, cudaStreamSynchronize(st));
+    if (misc[1] & 1) return fail(ctx, GD_EINVAL, "an edge of the batch leaves its graph's node range");
+    if (misc[1]) return fail(ctx, GD_EARITH, "inconsistent batch counts (status 0x%x)", misc[1]);
+    // graphs above the shared-memory limit: the single-graph path on a relabelled copy
+    if (misc[2] > 0) {
+        std::vector<int32_t> big((size_t)misc[2]);
+        GD_CK(ctx, cudaMemcpyAsync(big.data(), d_big, sizeof(int32_t) * big.size(), cudaMemcpyDeviceToHost, st));
+        GD_CK(ctx, cudaStreamSynchronize(st));
+        for (int32_t gi : big) {
+            const int32_t n0 = gnp[gi], n = gnp[gi + 1] - gnp[gi];
+            int32_t ends[2];
+            GD_CK(ctx, cudaMemcpyAsync(ends, d_rp + n0, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+            GD_CK(ctx, cudaMemcpyAsync(ends + 1, d_rp + n0 + n, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+            GD_CK(ctx, cudaStreamSynchronize(st));
+            const int64_t ne = ends[1] - ends[0];
+            PoolBlocks lb(ctx);
+            int32_t *lrp, *lci;
+            if ((rc = lb.get((void **)&lrp, sizeof(int32_t) * ((size_t)n + 1)))) return rc;
+            if ((rc = lb.get((void **)&lci, sizeof(int32_t) * (size_t)std::max<int64_t>(ne, 1)))) return rc;
+            GD_CK(ctx, launch_batch_slice(ctx, st, n0, n, d_rp, d_ci, lrp, lci));
+            gd_graph *sub = nullptr;
+            if ((rc = gd_create_csr(ctx, n, ne, lrp, lci, GD_DEVICE_PTRS | GD_BORROW, st, &sub))) return rc;
+            gd_u128 r[15];
+            rc = gd_count_global(sub, r);
+            gd_destroy_graph(sub);
+            if (rc) return rc;
+            uint64_t row[15];
+            for (int k = 0; k < 15; k++) {
+                if (r[k].hi) return fail(ctx, GD_EOVERFLOW, "graph %d: a count exceeds uint64", gi);
+                row[k] = r[k].lo;
+            }
+            GD_CK(ctx, cudaMemcpyAsync(d_out + (size_t)gi * 15, row, sizeof(row), cudaMemcpyHostToDevice, st));
+            GD_CK(ctx, cudaStreamSynchronize(st));
+        }
+    }
+    if (!dev_out) {
+        GD_CK(ctx, cudaMemcpyAsync(out, d_out, sizeof(uint64_t) * 15 * (size_t)num_graphs, cudaMemcpyDeviceToHost, st));
+    }
+    GD_CK(ctx, cudaStreamSynchronize(st));
+    return GD_OK;
 }
 
 int gd_profile_begin(gd_ctx *ctx) {

@@ -184,8 +184,12 @@ cudaError_t max_degree(gd_graph *g, int32_t *out_host);
 int32_t tribuf_warps(int sms);
 
 // batch (gd_batch.cu)
-int batch_count(gd_ctx *ctx, int32_t num_graphs, const int32_t *gnp, const int32_t *rp,
-                const int32_t *ci, int64_t nnz, int32_t ntot, uint64_t *out_dev);
+size_t batch_smem_bytes(int nmax);
+cudaError_t launch_batch_count(gd_ctx *ctx, cudaStream_t st, int32_t num_graphs, const int32_t *gnp,
+                               const int32_t *rp, const int32_t *ci, int32_t *work, unsigned long long *out,
+                               int32_t *gstatus, int32_t *big_list, int32_t *big_count, int nmax);
+cudaError_t launch_batch_slice(gd_ctx *ctx, cudaStream_t st, int32_t n0, int32_t n, const int32_t *rp,
+                               const int32_t *ci, int32_t *lrp, int32_t *lci);
 
 }  // namespace gdi
 

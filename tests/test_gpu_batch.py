@@ -1,0 +1,76 @@
+"""GPU parity of the batched path (gd_count_batch) against the CPU oracle:
+per-graph global counts, bit-exact, in one call."""
+import numpy as np
+import pytest
+
+from oracle import oracle
+from paper_1506_04322_gb300 import gd, inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = gd.Context(0)
+    yield c
+    c.close()
+
+
+def expected(graphs):
+    return np.array([oracle.alg2_global(g) for g in graphs], dtype=object)
+
+
+def check(ctx, graphs, **kw):
+    b = inputs.pack(graphs)
+    got = ctx.count_batch(b, **kw)
+    got = np.asarray(got).astype(np.uint64) if not hasattr(got, "cpu") else got.cpu().numpy().view(np.uint64)
+    want = expected(graphs)
+    for i, g in enumerate(graphs):
+        assert [int(x) for x in got[i]] == list(want[i]), (i, g.name)
+
+
+def test_batch_recipe_graphs(ctx):
+    """Graphs of the 20,000-graph recipe (ER and BA, n in [20, 500])."""
+    check(ctx, [inputs.batch_graph(i) for i in range(400)])
+
+
+def test_batch_edge_cases(ctx):
+    gs = [inputs.from_edges(0, []), inputs.from_edges(1, []), inputs.from_edges(2, [(0, 1)]),
+          inputs.from_edges(40, [(i, j) for i in range(40) for j in range(i + 1, 40)]),
+          inputs.from_edges(33, [(0, i) for i in range(1, 33)]),
+          inputs.erdos_renyi(512, 0.05, 3), inputs.erdos_renyi(513, 0.05, 4),   # 512-node variant edge
+          inputs.erdos_renyi(1024, 0.02, 5),
+          inputs.erdos_renyi(1100, 0.01, 6),          # above the shared-memory limit: single-graph path
+          inputs.from_edges(7, [])]
+    check(ctx, gs)
+
+
+def test_batch_device_pointers(ctx):
+    torch = pytest.importorskip("torch")
+    gs = [inputs.batch_graph(i, seed=9) for i in range(200)]
+    b = inputs.pack(gs)
+    db = inputs.PackedBatch(b.num_graphs, torch.from_numpy(b.graph_node_ptr).cuda(),
+                            torch.from_numpy(b.row_ptr).cuda(), torch.from_numpy(b.col_idx).cuda())
+    got = ctx.count_batch(db, device_out=True)
+    torch.cuda.synchronize()
+    got = got.cpu().numpy().view(np.uint64)
+    want = expected(gs)
+    for i in range(len(gs)):
+        assert [int(x) for x in got[i]] == list(want[i])
+
+
+def test_batch_repeated_calls(ctx):
+    gs = [inputs.batch_graph(i, seed=12) for i in range(300)]
+    b = inputs.pack(gs)
+    a1 = np.array(ctx.count_batch(b))
+    a2 = np.array(ctx.count_batch(b))
+    assert np.array_equal(a1, a2)
+
+
+def test_batch_rejects_edge_across_graphs(ctx):
+    # two graphs on nodes {0,1} and {2,3}; edge (1,2) crosses the boundary
+    g = inputs.from_edges(4, [(0, 1), (1, 2), (2, 3)])
+    b = inputs.PackedBatch(2, np.array([0, 2, 4], np.int32), g.row_ptr, g.col_idx)
+    with pytest.raises(gd.GDError) as ei:
+        ctx.count_batch(b)
+    assert ei.value.code == gd.GD_EINVAL
