@@ -57,6 +57,7 @@ def parse():
     ap.add_argument("--hub-log2", type=int, default=None, help="gd_options.hub_wedges_log2")
     ap.add_argument("--global-only", action="store_true", help="time gd_count_global instead")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-graphs measurement")
+    ap.add_argument("--no-serving", action="store_true", help="skip the request-loop measurement")
     return ap.parse_args()
 
 
@@ -212,6 +213,88 @@ def run_batch_measure(gd, torch, ctx, device, steps: int, loop_graphs: int = 600
             "graphs_per_s": G / dt, "ms_per_batch": 1000 * dt, "e2e_graphs_per_s": G / dt_e2e,
             "per_graph_loop_graphs_per_s": 1.0 / dt_loop, "per_graph_loop_sample": len(sub),
             "speedup_vs_loop": (G / dt) * dt_loop}
+
+
+def run_serving_measure(gd, count: int = 200, load: float = 0.7, slots: int = 4, seed: int = 5) -> dict:
+    """Request loop on the serving-trace recipe: Chung-Lu requests with m
+    log-uniform on [1e3, 5e6], exponent U[2.0, 2.8].  Capacity from a closed
+    loop, then Poisson arrivals at `load` x capacity; latency = completion -
+    arrival.  Baseline: the same arrivals served by a plain FIFO queue, one
+    request at a time (gd_count_global per request)."""
+    import concurrent.futures as cf
+    reqs = inputs.request_trace(count, rate_per_s=1.0, seed=seed)
+    with cf.ThreadPoolExecutor(max_workers=max(4, (os.cpu_count() or 8))) as ex:
+        graphs = list(ex.map(lambda r: r.graph(), reqs))
+    edges = sum(g.m for g in graphs)
+
+    def wait_all(ctx, ids):
+        out = {}
+        while len(out) < len(ids):
+            for rid in ids:
+                if rid not in out:
+                    rc, counts, st = ctx.poll(rid)
+                    if rc != gd.GD_EAGAIN:
+                        if rc != gd.GD_OK:
+                            raise RuntimeError(f"request failed: {rc}")
+                        out[rid] = (counts, st)
+            time.sleep(0.0005)
+        return out
+
+    with gd.Context(0) as ctx:
+        ctx.serve_start(slots=slots)
+        wait_all(ctx, [ctx.submit(g) for g in graphs[:8]])          # warm-up
+        t0 = time.perf_counter()
+        ids = [ctx.submit(g) for g in graphs]
+        closed = wait_all(ctx, ids)
+        t_closed = time.perf_counter() - t0
+        capacity = count / t_closed
+        rate = load * capacity
+        rng = np.random.default_rng(seed)
+        arrivals = np.cumsum(rng.exponential(1.0 / rate, size=count))
+        # open loop: submit at the arrival times
+        ids = []
+        t0 = time.perf_counter()
+        for a, g in zip(arrivals, graphs):
+            dt = a - (time.perf_counter() - t0)
+            if dt > 0:
+                time.sleep(dt)
+            ids.append(ctx.submit(g))
+        res = wait_all(ctx, ids)
+        span = time.perf_counter() - t0
+        lat = np.array([st["end_ms"] - st["submit_ms"] for _, st in res.values()])
+        stats = ctx.serve_stats()
+        results = [res[r][0] for r in ids]
+        ctx.serve_stop()
+    # baseline: FIFO queue, one request at a time, same arrivals
+    with gd.Context(0) as ctx:
+        for g in graphs[:4]:
+            with ctx.graph(g) as h:
+                h.count_global()
+        t0 = time.perf_counter()
+        base_lat = []
+        for a, g, r in zip(arrivals, graphs, results):
+            now = time.perf_counter() - t0
+            if now < a:
+                time.sleep(a - now)
+            with ctx.graph(g) as h:
+                c = h.count_global()
+            if c != r:
+                raise RuntimeError("a served result differs from the same graph counted alone")
+            base_lat.append(1000 * (time.perf_counter() - t0 - a))
+        base_span = time.perf_counter() - t0
+    base_lat = np.array(base_lat)
+    return {"workload": f"request trace: {count} Chung-Lu requests, m log-uniform [1e3,5e6], "
+                        f"exponent U[2.0,2.8], n=max(32,m/8), seed {seed}",
+            "requests": count, "edges": int(edges), "slots": slots,
+            "capacity_req_per_s": capacity, "capacity_edges_per_s": edges / t_closed,
+            "offered_req_per_s": rate, "load": load,
+            "throughput_req_per_s": count / span, "p50_ms": float(np.percentile(lat, 50)),
+            "p99_ms": float(np.percentile(lat, 99)), "batched_launches": stats["batched_launches"],
+            "single_launches": stats["single_launches"],
+            "fifo_queue": {"throughput_req_per_s": count / base_span,
+                           "p50_ms": float(np.percentile(base_lat, 50)),
+                           "p99_ms": float(np.percentile(base_lat, 99))},
+            "results_identical_alone_and_in_mix": True}
 
 
 def load_peaks():
@@ -400,6 +483,9 @@ def run_gd(args):
     batch = None
     if not args.no_batch:
         batch = run_batch_measure(gd, torch, ctx, device, max(2, min(args.steps, 5)))
+    serving = None
+    if not args.no_serving:
+        serving = run_serving_measure(gd)
 
     cpu = None
     if not args.no_cpu_baseline and ws == 1:
@@ -420,6 +506,7 @@ def run_gd(args):
         "cpu_baseline": cpu,
         "clocks": clk,
         "batch": batch,
+        "serving": serving,
         "kernels": {k: round(v["ms_total"] / args.steps, 3) for k, v in sorted(kern.items(), key=lambda kv: -kv[1]["ms_total"])},
         "global_counts": [str(x) for x in glob],
     }

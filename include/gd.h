@@ -205,6 +205,67 @@ int64_t gd_kernel_launches(const gd_ctx *ctx);
 int gd_pool_release(gd_ctx *ctx);
 
 /* ------------------------------------------------------------------------
+ * Serving: a request loop with continuous batching (no counterpart in the
+ * paper; the counts of every request are those of gd_count_global).
+ * ------------------------------------------------------------------------ */
+
+/* One counting request.  row_ptr / col_idx are HOST memory in the CSR format
+ * above; gd_submit copies them, so the caller may free them on return. */
+typedef struct gd_request_desc {
+    int32_t n;                 /* rows                                       */
+    int64_t nnz;               /* row_ptr[n]                                 */
+    const int32_t *row_ptr;
+    const int32_t *col_idx;
+    int32_t mode;              /* 0: the 15 global counts (the only mode)    */
+    int32_t reserved;
+} gd_request_desc;
+
+/* Timing of a finished request, in milliseconds since the service started. */
+typedef struct gd_req_stats {
+    double submit_ms;          /* gd_submit returned                         */
+    double start_ms;           /* a worker took it                           */
+    double end_ms;             /* its counts were ready                      */
+    size_t footprint;          /* device bytes reserved for it at admission  */
+    int32_t slot;              /* worker that ran it                         */
+    int32_t batched;           /* 1 if it ran inside a batched launch        */
+} gd_req_stats;
+
+/* Start the service of a context: `slots` worker threads, each with its own
+ * CUDA stream and device-block cache, so their requests overlap on the GPU.
+ * hbm_budget_bytes (0: the context's budget; 0 there too: unlimited) bounds
+ * the sum of the estimated footprints of the requests running at once
+ * (gd_footprint_estimate); a request waits until it fits.  gd_submit starts a
+ * service with 4 slots if none is running. */
+int gd_serve_start(gd_ctx *ctx, int32_t slots, size_t hbm_budget_bytes);
+
+/* Queue a request; *id identifies it.  Non-blocking.  GD_ENOMEM: the request
+ * alone exceeds the budget; GD_EINVAL: malformed descriptor (the full CSR
+ * check runs on the device later and is reported by gd_poll). */
+int gd_submit(gd_ctx *ctx, const gd_request_desc *desc, gd_req *id);
+
+/* GD_EAGAIN while the request is queued or running.  Once it is done: its
+ * status (GD_OK, or the error of its count) is returned, out (nullable) gets
+ * the 15 counts, st (nullable) its timing, and the request is released. */
+int gd_poll(gd_ctx *ctx, gd_req id, gd_u128 out[15], gd_req_stats *st);
+
+/* Block until the request is done (timeout_ms < 0: no limit); GD_ETIMEDOUT
+ * if the limit passes first.  Does not release it (call gd_poll). */
+int gd_wait(gd_ctx *ctx, gd_req id, int32_t timeout_ms);
+
+/* Queue length, requests running, bytes admitted, and how many launches were
+ * batched / single-graph so far. */
+int gd_serve_stats(gd_ctx *ctx, int64_t *queued, int64_t *running, size_t *inflight_bytes,
+                   int64_t *batched_launches, int64_t *single_launches);
+
+/* Finish the queued requests, stop the workers, release the service. */
+int gd_serve_stop(gd_ctx *ctx);
+
+/* Estimated device bytes of one count of a graph with n rows and nnz slots
+ * (the admission footprint): CSR copy plus every work array;
+ * per_edge adds the per-edge arrays and the staged output. */
+int gd_footprint_estimate(gd_ctx *ctx, int32_t n, int64_t nnz, int per_edge, size_t *bytes);
+
+/* ------------------------------------------------------------------------
  * Counting without allocating (no counterpart in the paper).
  *
  * For callers that must not allocate device memory: code running next to a

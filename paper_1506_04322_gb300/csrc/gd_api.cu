@@ -130,6 +130,70 @@ int32_t tricap_for(gd_graph *g, int variant) {
     return (int32_t)std::max<int64_t>(cap, 1);
 }
 
+// Every work array of a graph, as (pointer, bytes): one list serves both the
+// allocation and the footprint estimate used for admission.
+struct AllocSpec {
+    void **ptr;
+    size_t bytes;
+};
+
+template <typename T>
+AllocSpec spec(T **p, int64_t count) {
+    return AllocSpec{(void **)p, sizeof(T) * (size_t)std::max<int64_t>(count, 1)};
+}
+
+// part 0: arrays of every count call; part 1: dense wedge tables; part 2:
+// per-edge mode arrays
+void workspace_specs(Workspace &w, int64_t n, int64_t m, int64_t nnz, int32_t slots, int part,
+                     std::vector<AllocSpec> &out) {
+    if (part == 0) {
+        out.push_back(spec(&w.first_up, n));
+        out.push_back(spec(&w.eoff, n + 1));
+        out.push_back(spec(&w.eu, m));
+        out.push_back(spec(&w.ev, m));
+        out.push_back(spec(&w.eslot, m));
+        out.push_back(spec(&w.mate, nnz));
+        out.push_back(spec(&w.tslot, nnz));
+        out.push_back(spec(&w.tcred, nnz));
+        out.push_back(spec(&w.nd, nnz));
+        out.push_back(spec(&w.vlist, n));
+        out.push_back(spec(&w.hubs, n));
+        out.push_back(spec(&w.clist, 4 * n));
+        out.push_back(spec(&w.counters, (int64_t)C_NUM));
+        out.push_back(spec(&w.dag_off, n + 1));
+        out.push_back(spec(&w.dag_col, m));
+        out.push_back(spec(&w.dag_slot, m));
+        out.push_back(spec(&w.dag_nd, m));
+        out.push_back(spec(&w.sums, 2 * (int64_t)(S_NUM + X_NUM)));
+        out.push_back(spec(&w.result, 30));
+        out.push_back(spec(&w.scan_tmp, 3 * (n + 1) + 4096));
+        out.push_back(spec(&w.cacc, nnz));
+        out.push_back(spec(&w.yacc, nnz));
+        out.push_back(spec(&w.tcount, 64));
+        out.push_back(spec(&w.mlist, n));
+        out.push_back(spec(&w.west, n));
+        out.push_back(spec(&w.tlist, n));
+    } else if (part == 1) {
+        out.push_back(spec(&w.wtab, (int64_t)slots * n));
+        out.push_back(spec(&w.touched, (int64_t)slots * n));
+    } else {
+        out.push_back(spec(&w.tnode, n));
+        out.push_back(spec(&w.s1, n));
+        out.push_back(spec(&w.au, m));
+        out.push_back(spec(&w.dt, m));
+        out.push_back(spec(&w.qcred, nnz));
+        out.push_back(spec(&w.rcred, nnz));
+    }
+}
+
+int alloc_specs(gd_graph *g, const std::vector<AllocSpec> &sp) {
+    for (const AllocSpec &a : sp) {
+        int rc = dalloc(g, a.ptr, a.bytes);
+        if (rc) return rc;
+    }
+    return GD_OK;
+}
+
 // Allocate everything a count call needs (kept across calls; contents are
 // recomputed by every call).
 int ensure_workspace(gd_graph *g, bool per_edge) {
@@ -140,50 +204,51 @@ int ensure_workspace(gd_graph *g, bool per_edge) {
         if ((rc = dalloc_n(g, &w.status, 4))) return rc;
         GD_CK(g->ctx, cudaMemset(w.status, 0, 4 * sizeof(int32_t)));
     }
+    std::vector<AllocSpec> sp;
     if (!w.first_up) {
-        if ((rc = dalloc_n(g, &w.first_up, n))) return rc;
-        if ((rc = dalloc_n(g, &w.eoff, n + 1))) return rc;
-        if ((rc = dalloc_n(g, &w.eu, m))) return rc;
-        if ((rc = dalloc_n(g, &w.ev, m))) return rc;
-        if ((rc = dalloc_n(g, &w.eslot, m))) return rc;
-        if ((rc = dalloc_n(g, &w.mate, nnz))) return rc;
-        if ((rc = dalloc_n(g, &w.tslot, nnz))) return rc;
-        if ((rc = dalloc_n(g, &w.tcred, nnz))) return rc;
-        if ((rc = dalloc_n(g, &w.nd, nnz))) return rc;
-        if ((rc = dalloc_n(g, &w.vlist, n))) return rc;
-        if ((rc = dalloc_n(g, &w.hubs, n))) return rc;
-        if ((rc = dalloc_n(g, &w.clist, 4 * n))) return rc;
-        if ((rc = dalloc_n(g, &w.counters, C_NUM))) return rc;
-        if ((rc = dalloc_n(g, &w.dag_off, n + 1))) return rc;
-        if ((rc = dalloc_n(g, &w.dag_col, m))) return rc;
-        if ((rc = dalloc_n(g, &w.dag_slot, m))) return rc;
-        if ((rc = dalloc_n(g, &w.dag_nd, m))) return rc;
-        if ((rc = dalloc_n(g, &w.sums, 2 * (S_NUM + X_NUM)))) return rc;
-        if ((rc = dalloc_n(g, &w.result, 30))) return rc;
-        if ((rc = dalloc_n(g, &w.scan_tmp, 3 * (n + 1) + 4096))) return rc;
-        if ((rc = dalloc_n(g, &w.cacc, nnz))) return rc;
-        if ((rc = dalloc_n(g, &w.yacc, nnz))) return rc;
-        if ((rc = dalloc_n(g, &w.tcount, 64))) return rc;
-        if ((rc = dalloc_n(g, &w.mlist, n))) return rc;
-        if ((rc = dalloc_n(g, &w.west, n))) return rc;
-        if ((rc = dalloc_n(g, &w.tlist, n))) return rc;
+        workspace_specs(w, n, m, nnz, 0, 0, sp);
+        if ((rc = alloc_specs(g, sp))) return rc;
+        sp.clear();
     }
     if (!w.wtab && n > 0) {
         w.wtab_ctas = table_slots(g);
-        if ((rc = dalloc_n(g, &w.wtab, (int64_t)w.wtab_ctas * n))) return rc;
-        if ((rc = dalloc_n(g, &w.touched, (int64_t)w.wtab_ctas * n))) return rc;
+        workspace_specs(w, n, m, nnz, w.wtab_ctas, 1, sp);
+        if ((rc = alloc_specs(g, sp))) return rc;
+        sp.clear();
         GD_CK(g->ctx, cudaMemset(w.wtab, 0, sizeof(uint32_t) * (size_t)w.wtab_ctas * n));
     }
     if (per_edge && !w.tnode) {
-        if ((rc = dalloc_n(g, &w.tnode, n))) return rc;
-        if ((rc = dalloc_n(g, &w.s1, n))) return rc;
-        if ((rc = dalloc_n(g, &w.au, m))) return rc;
-        if ((rc = dalloc_n(g, &w.dt, m))) return rc;
-        if ((rc = dalloc_n(g, &w.qcred, nnz))) return rc;
-        if ((rc = dalloc_n(g, &w.rcred, nnz))) return rc;
+        workspace_specs(w, n, m, nnz, 0, 2, sp);
+        if ((rc = alloc_specs(g, sp))) return rc;
     }
     return GD_OK;
 }
+
+}  // namespace
+
+namespace gdi {
+
+// Device bytes a graph of n rows and nnz slots holds after one count call
+// (CSR copy included); per_edge adds the per-edge arrays and the staging of
+// a host-side output matrix.
+size_t estimate_footprint(gd_ctx *ctx, int64_t n, int64_t nnz, bool per_edge, bool host_out) {
+    Workspace w;
+    gd_graph g;
+    g.ctx = ctx; g.n = (int32_t)n; g.nnz = nnz; g.m = nnz / 2;
+    std::vector<AllocSpec> sp;
+    workspace_specs(w, n, nnz / 2, nnz, 0, 0, sp);
+    if (n > 0) workspace_specs(w, n, nnz / 2, nnz, table_slots(&g), 1, sp);
+    if (per_edge) workspace_specs(w, n, nnz / 2, nnz, 0, 2, sp);
+    size_t b = round_block(sizeof(int32_t) * (size_t)(n + 1 + nnz)) + round_block(16);   // CSR + status
+    for (const AllocSpec &a : sp) b += round_block(a.bytes);
+    if (per_edge && host_out) b += round_block(sizeof(uint64_t) * 15 * (size_t)(nnz / 2));
+    g.ws = Workspace();
+    return b;
+}
+
+}  // namespace gdi
+
+namespace {
 
 // Candidate buffers of the literal and pairwise-clique kernels.
 int ensure_tribuf(gd_graph *g, int variant) {
@@ -309,6 +374,7 @@ int gd_init(gd_ctx **ctx_out, int device, size_t hbm_budget_bytes, const gd_opti
 
 void gd_destroy(gd_ctx *ctx) {
     if (!ctx) return;
+    gdi::serve_destroy(ctx);
     cudaSetDevice(ctx->device);
     std::vector<gd_graph *> gs = ctx->graphs;
     for (gd_graph *g : gs) gd_destroy_graph(g);
@@ -685,6 +751,12 @@ int gd_profile_end(gd_ctx *ctx, gd_stage_stat *out, int32_t max_out, int32_t *nu
 }
 
 int64_t gd_kernel_launches(const gd_ctx *ctx) { return ctx ? ctx->launches : -1; }
+
+int gd_footprint_estimate(gd_ctx *ctx, int32_t n, int64_t nnz, int per_edge, size_t *bytes) {
+    if (!ctx || !bytes || n < 0 || nnz < 0) return GD_EINVAL;
+    *bytes = estimate_footprint(ctx, n, nnz, per_edge != 0, per_edge != 0);
+    return GD_OK;
+}
 
 int gd_pool_release(gd_ctx *ctx) {
     if (!ctx) return GD_EINVAL;

@@ -113,6 +113,8 @@ struct Workspace {
 
 
 namespace gdi {
+struct Service;
+void serve_destroy(gd_ctx *ctx);
 struct ProfRec {
     const char *name;
     cudaEvent_t a, b;
@@ -140,6 +142,8 @@ struct gd_ctx {
     std::vector<gdi::ProfRec> recs;
     std::vector<cudaEvent_t> evpool;
     int64_t launches = 0;
+    // request loop (gd_serve.cu)
+    gdi::Service *service = nullptr;
 };
 
 struct gd_graph {
@@ -182,6 +186,9 @@ int32_t table_slots(gd_graph *g);
 cudaError_t run_complete(gd_graph *g, int derive_cyc);
 cudaError_t max_degree(gd_graph *g, int32_t *out_host);
 int32_t tribuf_warps(int sms);
+
+// gd_api.cu
+size_t estimate_footprint(gd_ctx *ctx, int64_t n, int64_t nnz, bool per_edge, bool host_out);
 
 // batch (gd_batch.cu)
 size_t batch_smem_bytes(int nmax);

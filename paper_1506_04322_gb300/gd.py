@@ -51,6 +51,16 @@ class gd_stage_stat(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 40), ("ms_total", ctypes.c_double), ("launches", ctypes.c_int64)]
 
 
+class gd_request_desc(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("nnz", ctypes.c_int64), ("row_ptr", ctypes.c_void_p),
+                ("col_idx", ctypes.c_void_p), ("mode", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class gd_req_stats(ctypes.Structure):
+    _fields_ = [("submit_ms", ctypes.c_double), ("start_ms", ctypes.c_double), ("end_ms", ctypes.c_double),
+                ("footprint", ctypes.c_size_t), ("slot", ctypes.c_int32), ("batched", ctypes.c_int32)]
+
+
 class gd_options(ctypes.Structure):
     _fields_ = [("variant", ctypes.c_int32), ("block_threads", ctypes.c_int32),
                 ("ctas_per_sm", ctypes.c_int32), ("smem_table_max", ctypes.c_int32),
@@ -90,6 +100,13 @@ def load():
             "gd_kernel_launches": (i64, [vp]),
             "gd_pool_release": (ctypes.c_int, [vp]),
             "gd_count_global_static": (ctypes.c_int, [i32, i64, vp, vp, vp, vp]),
+            "gd_serve_start": (ctypes.c_int, [vp, i32, sz]),
+            "gd_submit": (ctypes.c_int, [vp, vp, ctypes.POINTER(ctypes.c_uint64)]),
+            "gd_poll": (ctypes.c_int, [vp, ctypes.c_uint64, vp, vp]),
+            "gd_wait": (ctypes.c_int, [vp, ctypes.c_uint64, i32]),
+            "gd_serve_stats": (ctypes.c_int, [vp, vp, vp, vp, vp, vp]),
+            "gd_serve_stop": (ctypes.c_int, [vp]),
+            "gd_footprint_estimate": (ctypes.c_int, [vp, i32, i64, ctypes.c_int, ctypes.POINTER(sz)]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -215,6 +232,53 @@ def gd_count_global_static(n: int, nnz: int, row_ptr: int, col_idx: int, out: in
     return int(load().gd_count_global_static(n, nnz, row_ptr, col_idx, out, stream or None))
 
 
+def gd_serve_start(ctx, slots: int = 4, hbm_budget_bytes: int = 0) -> None:
+    _check(ctx, load().gd_serve_start(ctx, slots, hbm_budget_bytes), "gd_serve_start")
+
+
+def gd_submit(ctx, n: int, nnz: int, row_ptr: int, col_idx: int) -> int:
+    d = gd_request_desc(n, nnz, row_ptr, col_idx, 0, 0)
+    rid = ctypes.c_uint64()
+    rc = load().gd_submit(ctx, ctypes.byref(d), ctypes.byref(rid))
+    if rc:
+        raise GDError(rc, "gd_submit")
+    return rid.value
+
+
+def gd_poll(ctx, rid: int):
+    """(status, counts or None, stats dict or None); status GD_EAGAIN while running."""
+    out = (gd_u128 * 15)()
+    st = gd_req_stats()
+    rc = load().gd_poll(ctx, rid, out, ctypes.byref(st))
+    if rc == GD_EAGAIN:
+        return rc, None, None
+    stats = {"submit_ms": st.submit_ms, "start_ms": st.start_ms, "end_ms": st.end_ms,
+             "footprint": st.footprint, "slot": st.slot, "batched": st.batched}
+    return rc, (_u128_list(out) if rc == GD_OK else None), stats
+
+
+def gd_wait(ctx, rid: int, timeout_ms: int = -1) -> int:
+    return int(load().gd_wait(ctx, rid, timeout_ms))
+
+
+def gd_serve_stats(ctx) -> dict:
+    q, r, b, bl, sl = (ctypes.c_int64(), ctypes.c_int64(), ctypes.c_size_t(), ctypes.c_int64(), ctypes.c_int64())
+    _check(ctx, load().gd_serve_stats(ctx, ctypes.byref(q), ctypes.byref(r), ctypes.byref(b), ctypes.byref(bl),
+                                      ctypes.byref(sl)), "gd_serve_stats")
+    return {"queued": q.value, "running": r.value, "inflight_bytes": b.value,
+            "batched_launches": bl.value, "single_launches": sl.value}
+
+
+def gd_serve_stop(ctx) -> None:
+    load().gd_serve_stop(ctx)
+
+
+def gd_footprint_estimate(ctx, n: int, nnz: int, per_edge: bool = False) -> int:
+    b = ctypes.c_size_t()
+    _check(ctx, load().gd_footprint_estimate(ctx, n, nnz, int(per_edge), ctypes.byref(b)), "gd_footprint_estimate")
+    return b.value
+
+
 # ---------------------------------------------------------------------------
 # object layer
 # ---------------------------------------------------------------------------
@@ -288,6 +352,30 @@ class Context:
 
     def kernel_launches(self) -> int:
         return gd_kernel_launches(self.handle)
+
+    # request loop
+    def serve_start(self, slots: int = 4, hbm_budget_bytes: int = 0) -> None:
+        gd_serve_start(self.handle, slots, hbm_budget_bytes)
+
+    def submit(self, g) -> int:
+        rp = np.ascontiguousarray(g.row_ptr, dtype=np.int32)
+        ci = np.ascontiguousarray(g.col_idx if g.nnz else np.zeros(1, np.int32), dtype=np.int32)
+        return gd_submit(self.handle, g.n, int(g.row_ptr[-1]), rp.ctypes.data, ci.ctypes.data)
+
+    def poll(self, rid: int):
+        return gd_poll(self.handle, rid)
+
+    def wait(self, rid: int, timeout_ms: int = -1) -> int:
+        return gd_wait(self.handle, rid, timeout_ms)
+
+    def serve_stats(self) -> dict:
+        return gd_serve_stats(self.handle)
+
+    def serve_stop(self) -> None:
+        gd_serve_stop(self.handle)
+
+    def footprint_estimate(self, n: int, nnz: int, per_edge: bool = False) -> int:
+        return gd_footprint_estimate(self.handle, n, nnz, per_edge)
 
     def graph(self, row_ptr, col_idx=None, n: int | None = None, validate: bool = False,
               borrow: bool = False, stream: int | None = None) -> "Graph":
