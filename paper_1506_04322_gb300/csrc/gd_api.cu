@@ -250,7 +250,26 @@ size_t estimate_footprint(gd_ctx *ctx, int64_t n, int64_t nnz, bool per_edge, bo
 
 namespace {
 
-// Candidate buffers of the literal and pairwise-clique kernels.
+// Per-CTA scratch of the large out-list clique kernel (out-lists above the
+// shared-memory limit), sized from the largest out-degree.
+int ensure_clique_scratch(gd_graph *g, const int32_t *cnt) {
+    Workspace &w = g->ws;
+    const int32_t dm = ((cnt[C_MAXDP] + 31) / 32) * 32;
+    const int32_t ctas = std::min<int32_t>(cnt[C_CL0 + 3], g->ctx->num_sms);
+    const size_t stride = (clique_big_bytes(dm) + 255) & ~(size_t)255;
+    const size_t need = stride * (size_t)ctas;
+    if (w.cbig && w.cbig_bytes >= need && w.cbig_dm >= dm) {
+        w.cbig_ctas = ctas;
+        return GD_OK;
+    }
+    if (w.cbig) { release_block(g, w.cbig); w.cbig = nullptr; }
+    int rc = dalloc(g, (void **)&w.cbig, need);
+    if (rc) return rc;
+    w.cbig_bytes = need; w.cbig_stride = stride; w.cbig_dm = dm; w.cbig_ctas = ctas;
+    return GD_OK;
+}
+
+// Candidate buffers of the literal kernel.
 int ensure_tribuf(gd_graph *g, int variant) {
     Workspace &w = g->ws;
     const int64_t need = (int64_t)tribuf_warps(g->ctx->num_sms) * tricap_for(g, variant) * 3;
@@ -520,21 +539,13 @@ static int count_path(gd_graph *g, bool per_edge, uint64_t *out_dev) {
     }
     int32_t cnt[C_NUM];
     GD_CK(ctx, run_schedule(g, cnt));
+    if (cnt[C_CL0 + 3] > 0 && (rc = ensure_clique_scratch(g, cnt))) return rc;
+    GD_CK(ctx, run_triangles_cliques(g, per_edge, cnt));
     bool cliq_credits = per_edge, qr_credits = false;
-    if (cnt[C_CL0 + 3] > 0) {
-        // an out-degree above the bitmap kernels' limit: pairwise clique tests
-        if ((rc = ensure_tribuf(g, variant))) return rc;
-        GD_CK(ctx, run_triangles_intersect(g));
-        GD_CK(ctx, run_cliques_pairwise(g));
-        cliq_credits = true;
-        if (per_edge) GD_CK(ctx, run_per_edge_sums(g));
-    } else {
-        GD_CK(ctx, run_triangles_cliques(g, per_edge, cnt));
-        if (per_edge) {
-            GD_CK(ctx, run_node_sums(g));
-            GD_CK(ctx, run_triangle_sums(g, cnt));
-            qr_credits = true;
-        }
+    if (per_edge) {
+        GD_CK(ctx, run_node_sums(g));
+        GD_CK(ctx, run_triangle_sums(g, cnt));
+        qr_credits = true;
     }
     GD_CK(ctx, run_cycles(g, per_edge, cnt));
     GD_CK(ctx, run_final(g, variant, per_edge, cliq_credits, qr_credits, out_dev));

@@ -230,80 +230,6 @@ __global__ void k_tri_sums(int64_t m, const int32_t *__restrict__ rp, const int3
 }
 
 // ---------------------------------------------------------------------------
-// Step 2, oriented: every 4-clique once, from the edge (a,b) of its two
-// lowest-ranked nodes; +1 on each of its six edges (slot credits).
-// ---------------------------------------------------------------------------
-__global__ void k_cliques_oriented(int64_t m, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
-                                   const int32_t *__restrict__ eu, const int32_t *__restrict__ ev,
-                                   const int32_t *__restrict__ eslot, const int32_t *__restrict__ mate,
-                                   int32_t *tribuf, int32_t tricap, unsigned long long *cacc, int32_t *status) {
-    const int lane = lane_id();
-    const int gw = global_warp();
-    int32_t *buf = tribuf + (int64_t)gw * tricap * 3;
-    for (int64_t k = gw; k < m; k += num_warps()) {
-        int32_t u = eu[k], v = ev[k];
-        int32_t du = rp[u + 1] - rp[u], dv = rp[v + 1] - rp[v];
-        int32_t p_uv = eslot[k];
-        // a precedes b
-        bool ua = precedes(du, u, dv, v);
-        int32_t a = ua ? u : v, b = ua ? v : u, db = ua ? dv : du;
-        int32_t p_ab = ua ? p_uv : mate[p_uv];
-        int32_t ba = rp[a], da = rp[a + 1] - ba, bb = rp[b];
-        // intersect N(a), N(b) (a has the smaller or equal degree)
-        int32_t cnt = 0;
-        for (int32_t i0 = 0; i0 < da; i0 += WARP) {
-            int32_t i = i0 + lane;
-            bool keep = false;
-            int32_t x = 0, j = -1;
-            if (i < da) {
-                x = ldg(ci + ba + i);
-                j = find_in(ci + bb, db, x);
-                if (j >= 0) {
-                    int32_t dx = rp[x + 1] - rp[x];
-                    keep = precedes(db, b, dx, x);
-                }
-            }
-            unsigned mask = __ballot_sync(0xffffffffu, keep);
-            int32_t pos = cnt + __popc(mask & ((1u << lane) - 1));
-            if (keep) {
-                if (pos < tricap) {
-                    buf[3 * pos] = x; buf[3 * pos + 1] = ba + i; buf[3 * pos + 2] = bb + j;
-                } else {
-                    atomicOr(status, ERR_CAPACITY);
-                }
-            }
-            cnt += __popc(mask);
-        }
-        __syncwarp();
-        if (cnt > tricap) cnt = tricap;
-        unsigned long long own = 0;
-        for (int32_t i = 0; i + 1 < cnt; i++) {
-            int32_t c = buf[3 * i], sac = buf[3 * i + 1], sbc = buf[3 * i + 2];
-            int32_t bc = rp[c], dc = rp[c + 1] - bc;
-            unsigned long long cc = 0;
-            for (int32_t j = i + 1 + lane; j < cnt; j += WARP) {
-                int32_t d = buf[3 * j];
-                int32_t q = find_in(ci + bc, dc, d);
-                if (q >= 0) {
-                    atomicAdd(cacc + (bc + q), 1ull);                 // (c,d)
-                    atomicAdd(cacc + buf[3 * j + 1], 1ull);           // (a,d)
-                    atomicAdd(cacc + buf[3 * j + 2], 1ull);           // (b,d)
-                    cc++;
-                }
-            }
-            cc = warp_sum(cc);
-            if (lane == 0 && cc) {
-                atomicAdd(cacc + sac, cc);    // (a,c)
-                atomicAdd(cacc + sbc, cc);    // (b,c)
-            }
-            own += cc;
-        }
-        if (lane == 0 && own) atomicAdd(cacc + p_ab, own);   // (a,b)
-        __syncwarp();
-    }
-}
-
-// ---------------------------------------------------------------------------
 // Step 2, literal (Algorithm 2 CliqueCount / CycleCount), warp per edge.
 // cliq_e: for w in Tri_e, r in N(w): r in Tri_e (each internal edge seen
 // twice; the paper's X(w)=0 reset halves it the same way).
@@ -673,22 +599,6 @@ cudaError_t run_literal(gd_graph *g) {
     const unsigned tri_blocks = (unsigned)(warps / (TRI_THREADS / 32));
     GD_LAUNCH(g, "k_literal", k_literal, tri_blocks, TRI_THREADS, 0, g->m, g->rp, g->ci, w.eu, w.ev, w.eslot,
               w.tribuf, tricap, (unsigned long long *)w.cacc, (unsigned long long *)w.yacc, w.status);
-    return cudaGetLastError();
-}
-
-// 4-clique credits by pairwise tests inside Tri+ (graphs whose largest
-// out-degree exceeds the bitmap kernels' limit).
-cudaError_t run_cliques_pairwise(gd_graph *g) {
-    Workspace &w = g->ws;
-    const int sms = sm_count(g);
-    if (g->m == 0) return cudaSuccess;
-    cudaError_t e = cudaMemsetAsync(w.cacc, 0, sizeof(uint64_t) * g->nnz, g->stream);
-    if (e) return e;
-    const int32_t warps = tribuf_warps(sms);
-    const int32_t tricap = (int32_t)(w.tribuf_words / ((int64_t)warps * 3));
-    const unsigned tri_blocks = (unsigned)(warps / (TRI_THREADS / 32));
-    GD_LAUNCH(g, "k_cliques_pairwise", k_cliques_oriented, tri_blocks, TRI_THREADS, 0, g->m, g->rp, g->ci, w.eu,
-              w.ev, w.eslot, w.mate, w.tribuf, tricap, (unsigned long long *)w.cacc, w.status);
     return cudaGetLastError();
 }
 

@@ -51,6 +51,7 @@ enum CounterIdx {
 constexpr int MB_BUCKETS = 40;
 constexpr int TINY_WEDGES = 256;   // warp-level wedge table of 2 * TINY_WEDGES entries
 constexpr int CL_D0 = 64, CL_D1 = 256, CL_D2 = 1024;
+constexpr int CL_BIG_THREADS = 512;   // CTA size of the large out-list (global scratch) variant
 constexpr long long HUB_MIN_WEDGES = 1ll << 18;
 
 // Device-side error bits (gdi::Status word).
@@ -86,6 +87,9 @@ struct Workspace {
     int32_t *dag_off = nullptr;    // [n+1] out-lists under the degree ordering
     int32_t *dag_col = nullptr, *dag_slot = nullptr, *dag_nd = nullptr;   // [m]
     uint32_t *tcred = nullptr;     // [nnz] triangle credits per slot
+    unsigned char *cbig = nullptr; // per-CTA scratch of the large out-list clique kernel
+    size_t cbig_bytes = 0, cbig_stride = 0;
+    int32_t cbig_dm = 0, cbig_ctas = 0;
     int32_t *touched = nullptr;    // [table slots * n] touched entries of the dense wedge tables
     int32_t *mlist = nullptr;      // [n] medium tier sorted by decreasing wedge work
     int32_t *tlist = nullptr;      // [n] tiny tier (warp per vertex)
@@ -173,7 +177,6 @@ cudaError_t prepare_edges(gd_graph *g);                   // edge list, reverse 
 cudaError_t run_triangles_intersect(gd_graph *g);         // |Tri| per slot by intersection
 cudaError_t run_per_edge_sums(gd_graph *g);               // t(x), S1(x), A_u, A_v, D_T
 cudaError_t run_literal(gd_graph *g);                     // Algorithm 2 CliqueCount / CycleCount
-cudaError_t run_cliques_pairwise(gd_graph *g);            // 4-clique credits, any out-degree
 cudaError_t run_final(gd_graph *g, int variant, bool per_edge, bool cliq_credits, bool qr_credits,
                       uint64_t *out_dev);
 // gd_step2.cu
@@ -181,6 +184,7 @@ cudaError_t run_schedule(gd_graph *g, int32_t *counters_host);
 cudaError_t run_triangles_cliques(gd_graph *g, bool per_edge, const int32_t *counters_host);
 cudaError_t run_triangle_sums(gd_graph *g, const int32_t *counters_host);   // Q/R credits (needs |Tri|)
 cudaError_t run_node_sums(gd_graph *g);                                      // t(x), S1(x)
+size_t clique_big_bytes(int32_t dm);                                         // per CTA
 cudaError_t run_cycles(gd_graph *g, bool per_edge, const int32_t *counters_host);
 int32_t table_slots(gd_graph *g);
 cudaError_t run_complete(gd_graph *g, int derive_cyc);

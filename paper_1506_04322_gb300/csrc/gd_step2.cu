@@ -95,7 +95,7 @@ __global__ void k_schedule(int32_t n, const int32_t *__restrict__ rp, const int3
             // clique buckets by out-degree (a node needs 2 out-neighbours to
             // be the lowest node of a triangle)
             if (dp >= 2) {
-                const int bkt = dp > cl_max ? 3 : dp <= CL_D0 ? 0 : dp <= CL_D1 ? 1 : 2;
+                const int bkt = (dp > cl_max || dp > CL_D2) ? 3 : dp <= CL_D0 ? 0 : dp <= CL_D1 ? 1 : 2;
                 const int32_t pos = atomicAdd(counters + C_CL0 + bkt, 1);
                 clist[(int64_t)bkt * n + pos] = u;
             }
@@ -165,7 +165,16 @@ struct CliqueArgs {
     unsigned long long *rcred;  // per-slot triangle degree-sum credits (triangle-sum mode)
     unsigned long long *sums;   // u128 sums (S_CLIQ gets 6 * K4 in global mode)
     int32_t *status;            // error bits
+    unsigned char *gstore;      // per-CTA work arrays of the large out-list variant
+    int32_t gdmax;              // its capacity (multiple of 32, >= largest out-degree)
+    size_t gstride;             // bytes per CTA
 };
+
+// Bytes of the large out-list variant's per-CTA work arrays.
+__host__ __device__ inline size_t clique_gstore_bytes(int32_t dm, int threads) {
+    const size_t W = (size_t)dm / 32;
+    return (size_t)dm * 48 + (size_t)dm * W * 4 + (size_t)(threads / 32) * W * 4 + 256;
+}
 
 template <int DMAX>
 struct CliqueSmem {
@@ -197,19 +206,46 @@ __device__ __forceinline__ int32_t out_slot(const CliqueArgs &a, int32_t x, int3
     return ldg(a.dag_slot + o + lo);
 }
 
+// Work arrays of one CTA: in shared memory (DMAX > 0) or in the CTA's slice
+// of global scratch (DMAX == 0: out-lists above the shared-memory limit).
+struct CliqueView {
+    int32_t *ids, *degs, *rank_of, *rid, *rslot, *rdeg;
+    uint32_t *cnt_p, *tri_p;
+    unsigned long long *qa, *ra;
+    uint32_t *M, *Sbuf;
+};
+
 template <int DMAX, int THREADS, int MODE>
 __global__ void __launch_bounds__(THREADS)
 k_clique_bitmap(CliqueArgs a) {
-    constexpr int W = DMAX / 32;
     constexpr int NW = THREADS / 32;
     extern __shared__ __align__(16) unsigned char smraw[];
-    CliqueSmem<DMAX> &S = *reinterpret_cast<CliqueSmem<DMAX> *>(smraw);
-    uint32_t *Sbuf = reinterpret_cast<uint32_t *>(smraw + sizeof(CliqueSmem<DMAX>));   // [NW][W]
+    CliqueView S;
+    int W;
+    if (DMAX > 0) {
+        CliqueSmem<(DMAX > 0 ? DMAX : 32)> &Sm = *reinterpret_cast<CliqueSmem<(DMAX > 0 ? DMAX : 32)> *>(smraw);
+        S.ids = Sm.ids; S.degs = Sm.degs; S.rank_of = Sm.rank_of; S.rid = Sm.rid; S.rslot = Sm.rslot;
+        S.rdeg = Sm.rdeg; S.cnt_p = Sm.cnt_p; S.tri_p = Sm.tri_p; S.qa = Sm.qa; S.ra = Sm.ra; S.M = Sm.M;
+        S.Sbuf = reinterpret_cast<uint32_t *>(smraw + sizeof(CliqueSmem<(DMAX > 0 ? DMAX : 32)>));
+        W = DMAX / 32;
+    } else {
+        const int32_t dm = a.gdmax;
+        unsigned char *base = a.gstore + (size_t)blockIdx.x * a.gstride;
+        S.qa = (unsigned long long *)base;
+        S.ra = S.qa + dm;
+        int32_t *p = (int32_t *)(S.ra + dm);
+        S.ids = p; S.degs = p + dm; S.rank_of = p + 2 * dm; S.rid = p + 3 * dm; S.rslot = p + 4 * dm;
+        S.rdeg = p + 5 * dm;
+        S.cnt_p = (uint32_t *)(p + 6 * dm); S.tri_p = S.cnt_p + dm;
+        S.M = S.tri_p + dm;
+        W = dm / 32;
+        S.Sbuf = S.M + (size_t)dm * W;
+    }
     const int lane = lane_id(), warp = threadIdx.x >> 5;
     const int32_t nv = a.counters[C_CL0 + a.bucket];
     const int32_t *list = a.clist + (int64_t)a.bucket * a.n;
     unsigned long long k4_local = 0;
-    uint32_t *mys = Sbuf + warp * W;
+    uint32_t *mys = S.Sbuf + warp * W;
 
     for (int32_t idx = blockIdx.x; idx < nv; idx += gridDim.x) {
         const int32_t va = list[idx];
@@ -828,13 +864,21 @@ static cudaError_t launch_clique(gd_graph *g, int bucket, int count) {
     a.cacc = (unsigned long long *)w.cacc; a.tcred = w.tcred; a.tslot = w.tslot;
     a.qcred = (unsigned long long *)w.qcred; a.rcred = (unsigned long long *)w.rcred;
     a.sums = w.sums; a.status = w.status;
-    const size_t smem = sizeof(CliqueSmem<DMAX>) + (size_t)(THREADS / 32) * (DMAX / 32) * 4;
-    cudaError_t e = allow_smem(k_clique_bitmap<DMAX, THREADS, MODE>, smem);
-    if (e) return e;
-    int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_clique_bitmap<DMAX, THREADS, MODE>, THREADS, smem);
-    if (e) return e;
-    const unsigned grid = grid_for(count, 1, sms_of(g) * (per_sm > 0 ? per_sm : 1));
+    a.gstore = w.cbig; a.gdmax = w.cbig_dm; a.gstride = w.cbig_stride;
+    const size_t smem = DMAX > 0 ? sizeof(CliqueSmem<(DMAX > 0 ? DMAX : 32)>) + (size_t)(THREADS / 32) * (DMAX / 32) * 4 : 0;
+    cudaError_t e;
+    unsigned grid;
+    if (DMAX > 0) {
+        e = allow_smem(k_clique_bitmap<DMAX, THREADS, MODE>, smem);
+        if (e) return e;
+        int per_sm = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_clique_bitmap<DMAX, THREADS, MODE>, THREADS, smem);
+        if (e) return e;
+        grid = grid_for(count, 1, sms_of(g) * (per_sm > 0 ? per_sm : 1));
+    } else {
+        grid = (unsigned)w.cbig_ctas;     // the global scratch holds this many CTAs
+        if (grid == 0) return cudaErrorInvalidValue;
+    }
     const char *name = MODE == MODE_TRISUM ? "k_trisum_bitmap" : "k_clique_bitmap";
     GD_LAUNCH(g, name, (k_clique_bitmap<DMAX, THREADS, MODE>), grid, THREADS, smem, a);
     return cudaGetLastError();
@@ -845,8 +889,11 @@ static cudaError_t launch_clique_buckets(gd_graph *g, const int32_t *cnt) {
     cudaError_t e;
     if ((e = launch_clique<CL_D0, 32, MODE>(g, 0, cnt[C_CL0]))) return e;
     if ((e = launch_clique<CL_D1, 128, MODE>(g, 1, cnt[C_CL0 + 1]))) return e;
-    return launch_clique<CL_D2, 512, MODE>(g, 2, cnt[C_CL0 + 2]);
+    if ((e = launch_clique<CL_D2, 512, MODE>(g, 2, cnt[C_CL0 + 2]))) return e;
+    return launch_clique<0, CL_BIG_THREADS, MODE>(g, 3, cnt[C_CL0 + 3]);
 }
+
+size_t clique_big_bytes(int32_t dm) { return clique_gstore_bytes(dm, CL_BIG_THREADS); }
 
 // Triangles per slot and 4-cliques (credits when per_edge).  Requires the
 // largest out-degree <= bitmap limit (checked by the caller).
