@@ -82,8 +82,14 @@ enum {
                             gd_destroy_graph) instead of copying them         */
 };
 
-/* gd_count_per_edge output flags */
+/* gd_count_per_edge / gd_count_batch output flags */
 enum { GD_OUT_DEVICE = 1 };
+
+/* gd_count_batch flag: keep the device part of the call (validation, the
+ * persistent counting launch, the result copy) as a captured CUDA graph and
+ * replay it when the next call has the same pointers, sizes and graph
+ * offsets.  Inputs must be device pointers (GD_DEVICE_PTRS). */
+enum { GD_CAPTURE = 8 };
 
 /* How the 4-node direct counts of Step 2 are obtained (Sec. 4.4). */
 typedef enum gd_variant {
@@ -116,6 +122,11 @@ typedef struct gd_options {
 
 /* Fill *opt with the defaults. */
 void gd_default_options(gd_options *opt);
+
+/* Replace a context's options (same checks as gd_init); the next count call
+ * uses them.  *opt receives nothing; gd_get_options reads them back. */
+int gd_set_options(gd_ctx *ctx, const gd_options *opt);
+int gd_get_options(const gd_ctx *ctx, gd_options *opt);
 
 /* Create a context on CUDA device `device`.  hbm_budget_bytes = 0: no limit;
  * otherwise graphs whose device footprint would exceed the budget are refused
@@ -203,6 +214,26 @@ int64_t gd_kernel_launches(const gd_ctx *ctx);
  * later graphs of the same shape (they count against the budget; a budget
  * refusal first releases them).  This call returns them to CUDA now. */
 int gd_pool_release(gd_ctx *ctx);
+
+/* ------------------------------------------------------------------------
+ * Autotuning (the paper's "auto-optimizer", Sec. 5.2, chooses data
+ * structures by graph density; here: the kernel cut-overs).
+ * ------------------------------------------------------------------------ */
+
+typedef struct gd_tune_result {
+    gd_options best;           /* fastest options found (now the context's)  */
+    double best_ms;            /* device time of one count with them        */
+    double default_ms;         /* device time with the options before tuning */
+    int32_t trials;            /* option sets timed                          */
+    int32_t reserved;
+} gd_tune_result;
+
+/* Time counts of g (per_edge != 0: gd_count_per_edge, else gd_count_global)
+ * under up to max_trials option sets -- shared-memory wedge table size,
+ * bitmap out-degree limit, hub wedge threshold -- with CUDA events on the
+ * graph's stream, and make the fastest the context's options.  The counts
+ * are identical under every option set; only the time differs. */
+int gd_autotune(gd_graph *g, int per_edge, int32_t max_trials, gd_tune_result *res);
 
 /* ------------------------------------------------------------------------
  * Serving: a request loop with continuous batching (no counterpart in the

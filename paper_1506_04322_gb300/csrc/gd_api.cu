@@ -339,6 +339,31 @@ void prof_end(gd_ctx *c, cudaStream_t st) {
     cudaEventRecord(c->recs.back().b, st);
 }
 
+struct BatchGraph {
+    int32_t G = 0, N = 0;
+    int64_t nnz = 0;
+    const void *gnp = nullptr, *rp = nullptr, *ci = nullptr;
+    void *out = nullptr;
+    std::vector<int32_t> gnp_host;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int32_t *d_misc = nullptr, *d_big = nullptr;
+    size_t misc_bytes = 0, big_bytes = 0;
+    int32_t *h_status = nullptr;      // pinned
+};
+
+void batch_graph_destroy(gd_ctx *ctx) {
+    BatchGraph *b = ctx->bgraph;
+    if (!b) return;
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    if (b->d_misc) ctx_release(ctx, b->d_misc, b->misc_bytes);
+    if (b->d_big) ctx_release(ctx, b->d_big, b->big_bytes);
+    if (b->h_status) cudaFreeHost(b->h_status);
+    delete b;
+    ctx->bgraph = nullptr;
+}
+
 }  // namespace gdi
 
 extern "C" {
@@ -354,6 +379,32 @@ void gd_default_options(gd_options *opt) {
     opt->hub_wedges_log2 = 21;
 }
 
+static int check_options(gd_options *o) {
+    const int t = o->smem_table_max;
+    if (t < 256 || t > 16384 || (t & (t - 1))) return GD_EINVAL;
+    if (o->variant < 0 || o->variant > 2) return GD_EINVAL;
+    if (o->bitmap_max_outdeg == 0) o->bitmap_max_outdeg = gdi::CL_D2;
+    if (o->hub_wedges_log2 == 0) o->hub_wedges_log2 = 21;
+    if (o->bitmap_max_outdeg < 2 || o->bitmap_max_outdeg > gdi::CL_D2 || o->hub_wedges_log2 < 4 ||
+        o->hub_wedges_log2 > 40) return GD_EINVAL;
+    return GD_OK;
+}
+
+int gd_set_options(gd_ctx *ctx, const gd_options *opt) {
+    if (!ctx || !opt) return GD_EINVAL;
+    gd_options o = *opt;
+    int rc = check_options(&o);
+    if (rc) return fail(ctx, rc, "invalid options");
+    ctx->opt = o;
+    return GD_OK;
+}
+
+int gd_get_options(const gd_ctx *ctx, gd_options *opt) {
+    if (!ctx || !opt) return GD_EINVAL;
+    *opt = ctx->opt;
+    return GD_OK;
+}
+
 int gd_init(gd_ctx **ctx_out, int device, size_t hbm_budget_bytes, const gd_options *opt) {
     if (!ctx_out) return GD_EINVAL;
     *ctx_out = nullptr;
@@ -364,17 +415,7 @@ int gd_init(gd_ctx **ctx_out, int device, size_t hbm_budget_bytes, const gd_opti
     gd_default_options(&ctx->opt);
     if (opt) {
         ctx->opt = *opt;
-        int t = ctx->opt.smem_table_max;
-        if (t < 256 || t > 16384 || (t & (t - 1))) {
-            int rc = fail(ctx, GD_EINVAL, "smem_table_max must be a power of two in [256, 16384]");
-            delete ctx;
-            return rc;
-        }
-        if (ctx->opt.variant < 0 || ctx->opt.variant > 2) { delete ctx; return GD_EINVAL; }
-        if (ctx->opt.bitmap_max_outdeg == 0) ctx->opt.bitmap_max_outdeg = gdi::CL_D2;
-        if (ctx->opt.hub_wedges_log2 == 0) ctx->opt.hub_wedges_log2 = 21;
-        if (ctx->opt.bitmap_max_outdeg < 2 || ctx->opt.bitmap_max_outdeg > gdi::CL_D2 ||
-            ctx->opt.hub_wedges_log2 < 4 || ctx->opt.hub_wedges_log2 > 40) {
+        if (check_options(&ctx->opt)) {
             delete ctx;
             return GD_EINVAL;
         }
@@ -395,6 +436,7 @@ void gd_destroy(gd_ctx *ctx) {
     if (!ctx) return;
     gdi::serve_destroy(ctx);
     cudaSetDevice(ctx->device);
+    gdi::batch_graph_destroy(ctx);
     std::vector<gd_graph *> gs = ctx->graphs;
     for (gd_graph *g : gs) gd_destroy_graph(g);
     if (ctx->batch_buf) cudaFree(ctx->batch_buf);
@@ -600,6 +642,62 @@ struct PoolBlocks {
     ~PoolBlocks() { for (auto &b : bl) ctx_release(ctx, b.first, b.second); }
 };
 
+// The device part of a batch call as a captured CUDA graph: zero the work
+// words, validate the packed union, count (one persistent launch), copy the
+// status words to pinned host memory.  Replayed while the call is the same.
+static int count_batch_captured(gd_ctx *ctx, int32_t G, const std::vector<int32_t> &gnp, int32_t N, int64_t nnz,
+                                int32_t nmax_graph, const int32_t *d_gnp, const int32_t *d_rp, const int32_t *d_ci,
+                                uint64_t *d_out) {
+    cudaStream_t st = ctx->stream;
+    BatchGraph *b = ctx->bgraph;
+    const bool same = b && b->G == G && b->N == N && b->nnz == nnz && b->gnp == d_gnp && b->rp == d_rp &&
+                      b->ci == d_ci && b->out == d_out && b->gnp_host == gnp;
+    if (!same) {
+        batch_graph_destroy(ctx);
+        b = new (std::nothrow) BatchGraph();
+        if (!b) return fail(ctx, GD_ENOMEM, "host allocation failed");
+        ctx->bgraph = b;
+        b->G = G; b->N = N; b->nnz = nnz; b->gnp = d_gnp; b->rp = d_rp; b->ci = d_ci; b->out = d_out;
+        b->gnp_host = gnp;
+        b->misc_bytes = 64 * sizeof(int32_t);
+        b->big_bytes = sizeof(int32_t) * (size_t)G;
+        int rc;
+        if ((rc = ctx_alloc(ctx, (void **)&b->d_misc, b->misc_bytes))) { batch_graph_destroy(ctx); return rc; }
+        if ((rc = ctx_alloc(ctx, (void **)&b->d_big, b->big_bytes))) { batch_graph_destroy(ctx); return rc; }
+        GD_CK(ctx, cudaHostAlloc((void **)&b->h_status, 64 * sizeof(int32_t), cudaHostAllocDefault));
+        gd_graph tmp;
+        tmp.ctx = ctx; tmp.stream = st; tmp.n = N; tmp.nnz = nnz; tmp.m = nnz / 2;
+        tmp.rp = const_cast<int32_t *>(d_rp); tmp.ci = const_cast<int32_t *>(d_ci);
+        const bool prof = ctx->prof;
+        ctx->prof = false;      // no event records inside the capture
+        cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) e = cudaMemsetAsync(b->d_misc, 0, b->misc_bytes, st);
+        if (e == cudaSuccess) e = launch_validate(&tmp, b->d_misc + 8);
+        if (e == cudaSuccess)
+            e = launch_batch_count(ctx, st, G, d_gnp, d_rp, d_ci, b->d_misc, (unsigned long long *)d_out,
+                                   b->d_misc + 1, b->d_big, b->d_misc + 2, nmax_graph <= 512 ? 512 : 1024);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(b->h_status, b->d_misc, 16 * sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+        cudaGraph_t graph = nullptr;
+        cudaError_t e2 = cudaStreamEndCapture(st, &graph);
+        ctx->prof = prof;
+        tmp.ws = Workspace();
+        if (e == cudaSuccess) e = e2;
+        if (e != cudaSuccess) { if (graph) cudaGraphDestroy(graph); batch_graph_destroy(ctx); return cuda_fail(ctx, e, "batch capture"); }
+        b->graph = graph;
+        e = cudaGraphInstantiate(&b->exec, graph, 0);
+        if (e != cudaSuccess) { batch_graph_destroy(ctx); return cuda_fail(ctx, e, "batch graph instantiate"); }
+    }
+    GD_CK(ctx, cudaGraphLaunch(b->exec, st));
+    GD_CK(ctx, cudaStreamSynchronize(st));
+    const int32_t *h = b->h_status;
+    if (h[8]) return fail(ctx, GD_EINVAL, "invalid batch CSR: rows must be strictly ascending, ids in range, "
+                          "no self-loops, every edge stored in both directions");
+    if (h[1] & 1) return fail(ctx, GD_EINVAL, "an edge of the batch leaves its graph's node range");
+    if (h[1]) return fail(ctx, GD_EARITH, "inconsistent batch counts (status 0x%x)", h[1]);
+    return GD_OK;
+}
+
 int gd_count_batch(gd_ctx *ctx, int32_t num_graphs, const int32_t *graph_node_ptr, const int32_t *row_ptr,
                    const int32_t *col_idx, int flags, uint64_t *out) {
     if (!ctx) return GD_EINVAL;
@@ -642,6 +740,8 @@ int gd_count_batch(gd_ctx *ctx, int32_t num_graphs, const int32_t *graph_node_pt
     const int64_t nnz = nnz32;
     if (nnz < 0 || (nnz & 1)) return fail(ctx, GD_EINVAL, "row_ptr[N] must be a non-negative even count");
     if (nnz > 0 && !col_idx) return fail(ctx, GD_EINVAL, "null col_idx");
+    if ((flags & GD_CAPTURE) && dev && dev_out && nmax_graph <= 1024)
+        return count_batch_captured(ctx, num_graphs, gnp, N, nnz, nmax_graph, graph_node_ptr, row_ptr, col_idx, out);
     PoolBlocks pb(ctx);
     int rc;
     const int32_t *d_gnp = graph_node_ptr, *d_rp = row_ptr, *d_ci = col_idx;
@@ -721,6 +821,71 @@ int gd_count_batch(gd_ctx *ctx, int32_t num_graphs, const int32_t *graph_node_pt
         GD_CK(ctx, cudaMemcpyAsync(out, d_out, sizeof(uint64_t) * 15 * (size_t)num_graphs, cudaMemcpyDeviceToHost, st));
     }
     GD_CK(ctx, cudaStreamSynchronize(st));
+    return GD_OK;
+}
+
+int gd_autotune(gd_graph *g, int per_edge, int32_t max_trials, gd_tune_result *res) {
+    if (!g || !res) return GD_EINVAL;
+    gd_ctx *ctx = g->ctx;
+    ctx->err.clear();
+    GD_CK(ctx, cudaSetDevice(ctx->device));
+    const gd_options start = ctx->opt;
+    uint64_t *out = nullptr;
+    int rc;
+    if (per_edge) {
+        const size_t bytes = sizeof(uint64_t) * 15 * (size_t)g->m;
+        if (!g->ws.out_buf || g->ws.out_buf_bytes < bytes) {
+            if (g->ws.out_buf) { release_block(g, g->ws.out_buf); g->ws.out_buf = nullptr; }
+            if ((rc = dalloc(g, (void **)&g->ws.out_buf, bytes))) return rc;
+            g->ws.out_buf_bytes = bytes;
+        }
+        out = g->ws.out_buf;
+    }
+    cudaEvent_t e0, e1;
+    GD_CK(ctx, cudaEventCreate(&e0));
+    GD_CK(ctx, cudaEventCreate(&e1));
+    auto time_once = [&](double *ms) -> int {
+        // two runs: the first settles allocations and caches, the second is timed
+        for (int r = 0; r < 2; r++) {
+            GD_CK(ctx, cudaEventRecord(e0, g->stream));
+            int rc2 = count_path(g, per_edge != 0, out);
+            if (rc2) return rc2;
+            GD_CK(ctx, cudaEventRecord(e1, g->stream));
+            if ((rc2 = read_results(g, nullptr))) return rc2;
+            float f = 0.f;
+            GD_CK(ctx, cudaEventElapsedTime(&f, e0, e1));
+            *ms = f;
+        }
+        return GD_OK;
+    };
+    double best_ms = 0;
+    if ((rc = time_once(&best_ms))) { ctx->opt = start; return rc; }
+    res->default_ms = best_ms;
+    gd_options best = start;
+    int32_t trials = 1;
+    const int32_t smem_c[] = {4096, 8192, 16384};
+    const int32_t bitmap_c[] = {256, 1024};
+    const int32_t hub_c[] = {18, 21, 24, 40};
+    for (int32_t sm : smem_c)
+        for (int32_t bm : bitmap_c)
+            for (int32_t hb : hub_c) {
+                if (trials >= max_trials) break;
+                gd_options o = start;
+                o.smem_table_max = sm; o.bitmap_max_outdeg = bm; o.hub_wedges_log2 = hb;
+                if (o.smem_table_max == start.smem_table_max && o.bitmap_max_outdeg == start.bitmap_max_outdeg &&
+                    o.hub_wedges_log2 == start.hub_wedges_log2) continue;
+                ctx->opt = o;
+                double ms = 0;
+                if ((rc = time_once(&ms))) { ctx->opt = start; cudaEventDestroy(e0); cudaEventDestroy(e1); return rc; }
+                trials++;
+                if (ms < best_ms) { best_ms = ms; best = o; }
+            }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    ctx->opt = best;
+    res->best = best;
+    res->best_ms = best_ms;
+    res->trials = trials;
     return GD_OK;
 }
 

@@ -510,6 +510,11 @@ cudaError_t max_degree(gd_graph *g, int32_t *out_host) {
     return cudaMemsetAsync(w.status + 3, 0, sizeof(int32_t), st);
 }
 
+cudaError_t launch_validate(gd_graph *g, int32_t *status) {
+    if (g->n > 0) GD_LAUNCH(g, "k_validate", k_validate, grid_for((int64_t)g->n * 32, 256, sm_count(g) * 16), 256, 0, g->n, g->nnz, g->rp, g->ci, status);
+    return cudaGetLastError();
+}
+
 cudaError_t validate_csr(gd_graph *g, int32_t *bad_index, int32_t *bad_code) {
     Workspace &w = g->ws;
     cudaStream_t st = g->stream;

@@ -118,6 +118,8 @@ struct Workspace {
 
 namespace gdi {
 struct Service;
+struct BatchGraph;      // captured CUDA graph of gd_count_batch (gd_api.cu)
+void batch_graph_destroy(gd_ctx *ctx);
 void serve_destroy(gd_ctx *ctx);
 struct ProfRec {
     const char *name;
@@ -148,6 +150,8 @@ struct gd_ctx {
     int64_t launches = 0;
     // request loop (gd_serve.cu)
     gdi::Service *service = nullptr;
+    // captured batch pipeline
+    gdi::BatchGraph *bgraph = nullptr;
 };
 
 struct gd_graph {
@@ -173,6 +177,7 @@ void prof_end(gd_ctx *c, cudaStream_t st);
 
 // kernels (gd_count.cu)
 cudaError_t validate_csr(gd_graph *g, int32_t *bad_index_host, int32_t *bad_code_host);
+cudaError_t launch_validate(gd_graph *g, int32_t *status);   // kernel only (capturable)
 cudaError_t prepare_edges(gd_graph *g);                   // edge list, reverse slots, zero sums
 cudaError_t run_triangles_intersect(gd_graph *g);         // |Tri| per slot by intersection
 cudaError_t run_per_edge_sums(gd_graph *g);               // t(x), S1(x), A_u, A_v, D_T

@@ -34,6 +34,7 @@ STATUS_NAMES = {0: "GD_OK", 1: "GD_EINVAL", 2: "GD_ENOMEM", 3: "GD_ECUDA", 4: "G
                 5: "GD_ETIMEDOUT", 6: "GD_EOVERFLOW", 7: "GD_ENOTIMPL", 8: "GD_EARITH"}
 GD_DEVICE_PTRS, GD_VALIDATE, GD_BORROW = 1, 2, 4
 GD_OUT_DEVICE = 1
+GD_CAPTURE = 8
 GD_VARIANT_AUTO, GD_VARIANT_LITERAL, GD_VARIANT_ORIENTED = 0, 1, 2
 
 
@@ -66,6 +67,11 @@ class gd_options(ctypes.Structure):
                 ("ctas_per_sm", ctypes.c_int32), ("smem_table_max", ctypes.c_int32),
                 ("bitmap_max_outdeg", ctypes.c_int32), ("hub_wedges_log2", ctypes.c_int32),
                 ("reserved", ctypes.c_int32 * 6)]
+
+
+class gd_tune_result(ctypes.Structure):
+    _fields_ = [("best", gd_options), ("best_ms", ctypes.c_double), ("default_ms", ctypes.c_double),
+                ("trials", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 _lib = None
@@ -107,6 +113,9 @@ def load():
             "gd_serve_stats": (ctypes.c_int, [vp, vp, vp, vp, vp, vp]),
             "gd_serve_stop": (ctypes.c_int, [vp]),
             "gd_footprint_estimate": (ctypes.c_int, [vp, i32, i64, ctypes.c_int, ctypes.POINTER(sz)]),
+            "gd_autotune": (ctypes.c_int, [vp, ctypes.c_int, i32, vp]),
+            "gd_set_options": (ctypes.c_int, [vp, vp]),
+            "gd_get_options": (ctypes.c_int, [vp, vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -232,6 +241,15 @@ def gd_count_global_static(n: int, nnz: int, row_ptr: int, col_idx: int, out: in
     return int(load().gd_count_global_static(n, nnz, row_ptr, col_idx, out, stream or None))
 
 
+def gd_autotune(ctx, graph, per_edge: bool = False, max_trials: int = 24) -> dict:
+    r = gd_tune_result()
+    _check(ctx, load().gd_autotune(graph, int(per_edge), max_trials, ctypes.byref(r)), "gd_autotune")
+    b = r.best
+    return {"smem_table_max": b.smem_table_max, "bitmap_max_outdeg": b.bitmap_max_outdeg,
+            "hub_wedges_log2": b.hub_wedges_log2, "best_ms": r.best_ms, "default_ms": r.default_ms,
+            "trials": r.trials}
+
+
 def gd_serve_start(ctx, slots: int = 4, hbm_budget_bytes: int = 0) -> None:
     _check(ctx, load().gd_serve_start(ctx, slots, hbm_budget_bytes), "gd_serve_start")
 
@@ -321,6 +339,7 @@ class Context:
         if hub_wedges_log2:
             o.hub_wedges_log2 = hub_wedges_log2
         self.handle = gd_init(device, hbm_budget_bytes, o)
+        self.variant = variant
         self._graphs = []
 
     def close(self):
@@ -343,6 +362,14 @@ class Context:
     @property
     def last_error(self) -> str:
         return gd_last_error(self.handle)
+
+    def set_options(self, o: gd_options) -> None:
+        _check(self.handle, load().gd_set_options(self.handle, ctypes.byref(o)), "gd_set_options")
+
+    def options(self) -> gd_options:
+        o = gd_options()
+        _check(self.handle, load().gd_get_options(self.handle, ctypes.byref(o)), "gd_get_options")
+        return o
 
     def profile_begin(self) -> None:
         gd_profile_begin(self.handle)
@@ -403,7 +430,8 @@ class Context:
         gr = Graph(self, h, keep if borrow else None)
         return gr
 
-    def count_batch(self, batch, out=None, validate: bool = False, device_out: bool = False):
+    def count_batch(self, batch, out=None, validate: bool = False, device_out: bool = False,
+                    capture: bool = False):
         """Per-graph global counts of a packed batch (inputs.PackedBatch or
         arrays/tensors graph_node_ptr, row_ptr, col_idx).  Returns a uint64
         array [G, 15] (numpy, or the given/allocated torch tensor)."""
@@ -422,6 +450,8 @@ class Context:
         po, odev = _ptr(out)
         if odev:
             flags |= GD_OUT_DEVICE
+        if capture:
+            flags |= GD_CAPTURE
         gd_count_batch(self.handle, G, pg, pr, pc, flags, po)
         return out[:G]
 
@@ -446,6 +476,10 @@ class Graph:
 
     def footprint(self) -> int:
         return gd_graph_footprint(self.handle)
+
+    def autotune(self, per_edge: bool = False, max_trials: int = 24) -> dict:
+        """Time option sets on this graph; the fastest become the context's."""
+        return gd_autotune(self.ctx.handle, self.handle, per_edge, max_trials)
 
     def count_global(self) -> list[int]:
         return gd_count_global(self.ctx.handle, self.handle)

@@ -74,3 +74,29 @@ def test_batch_rejects_edge_across_graphs(ctx):
     with pytest.raises(gd.GDError) as ei:
         ctx.count_batch(b)
     assert ei.value.code == gd.GD_EINVAL
+
+
+def test_batch_captured_graph_replays(ctx):
+    """GD_CAPTURE: the device part runs as a captured CUDA graph, replayed
+    while the call is unchanged and re-captured when the offsets change."""
+    torch = pytest.importorskip("torch")
+    gs = [inputs.batch_graph(i, seed=21) for i in range(150)]
+    b = inputs.pack(gs)
+    db = inputs.PackedBatch(b.num_graphs, torch.from_numpy(b.graph_node_ptr).cuda(),
+                            torch.from_numpy(b.row_ptr).cuda(), torch.from_numpy(b.col_idx).cuda())
+    out = torch.empty((b.num_graphs, 15), dtype=torch.int64, device="cuda")
+    want = np.array(ctx.count_batch(b))
+    for _ in range(3):
+        out.fill_(-1)
+        ctx.count_batch(db, out=out, capture=True)
+        torch.cuda.synchronize()
+        assert np.array_equal(out.cpu().numpy().view(np.uint64), want)
+    # another batch in the same buffers' shape but different graphs: re-captured
+    gs2 = [inputs.batch_graph(i, seed=22) for i in range(150)]
+    b2 = inputs.pack(gs2)
+    db2 = inputs.PackedBatch(b2.num_graphs, torch.from_numpy(b2.graph_node_ptr).cuda(),
+                             torch.from_numpy(b2.row_ptr).cuda(), torch.from_numpy(b2.col_idx).cuda())
+    out2 = torch.empty((b2.num_graphs, 15), dtype=torch.int64, device="cuda")
+    ctx.count_batch(db2, out=out2, capture=True)
+    torch.cuda.synchronize()
+    assert np.array_equal(out2.cpu().numpy().view(np.uint64), np.array(ctx.count_batch(b2)))

@@ -226,3 +226,19 @@ def test_rmat_workload_global(ctxs):
     with ctxs[gd.GD_VARIANT_ORIENTED].graph(g) as h:
         glob = h.count_global()
     assert glob == [int(x) for x in rec["global"]]
+
+
+def test_autotune_keeps_counts_and_caches(tmp_path):
+    from paper_1506_04322_gb300 import autotune
+    g = inputs.chung_lu(60_000, 2.1, 420_000, 0.0, 31)
+    with gd.Context(0) as ctx, ctx.graph(g) as h:
+        before = h.count_global()
+        pe_before, _ = h.count_per_edge()
+        cache = str(tmp_path / "tune.json")
+        r = autotune.tuned_options(ctx, h, g, per_edge=False, cache_path=cache, max_trials=6)
+        assert not r["cached"] and r["trials"] >= 2 and r["best_ms"] <= r["default_ms"]
+        assert h.count_global() == before
+        assert np.array_equal(h.count_per_edge()[0], pe_before)
+        r2 = autotune.tuned_options(ctx, h, g, per_edge=False, cache_path=cache)
+        assert r2["cached"] and r2["options"] == r["options"]
+        assert h.count_global() == before
