@@ -269,6 +269,24 @@ int ensure_clique_scratch(gd_graph *g, const int32_t *cnt) {
     return GD_OK;
 }
 
+// Flat neighbour lists of a hub batch: lengths, prefix, scan scratch.
+int ensure_hub_scratch(gd_graph *g) {
+    Workspace &w = g->ws;
+    const int64_t cap = (int64_t)hub_batch(g) * std::max<int32_t>(g->max_deg, 1);
+    if (w.hub_off && w.hub_flat_cap >= cap) return GD_OK;
+    int rc;
+    if (w.hub_off) {
+        release_block(g, w.hub_off); release_block(g, w.hub_len); release_block(g, w.hub_pre);
+        release_block(g, w.hub_scan_tmp);
+    }
+    if ((rc = dalloc_n(g, &w.hub_off, 64))) return rc;
+    if ((rc = dalloc_n(g, &w.hub_len, cap))) return rc;
+    if ((rc = dalloc_n(g, &w.hub_pre, cap + 1))) return rc;
+    if ((rc = dalloc_n(g, &w.hub_scan_tmp, 2 * (cap / 2048 + 1) + 4096))) return rc;
+    w.hub_flat_cap = cap;
+    return GD_OK;
+}
+
 // Candidate buffers of the literal kernel.
 int ensure_tribuf(gd_graph *g, int variant) {
     Workspace &w = g->ws;
@@ -582,6 +600,7 @@ static int count_path(gd_graph *g, bool per_edge, uint64_t *out_dev) {
     int32_t cnt[C_NUM];
     GD_CK(ctx, run_schedule(g, cnt));
     if (cnt[C_CL0 + 3] > 0 && (rc = ensure_clique_scratch(g, cnt))) return rc;
+    if (cnt[C_HUB] > 0 && (rc = ensure_hub_scratch(g))) return rc;
     GD_CK(ctx, run_triangles_cliques(g, per_edge, cnt));
     bool cliq_credits = per_edge, qr_credits = false;
     if (per_edge) {

@@ -92,6 +92,8 @@ struct Workspace {
     int32_t cbig_dm = 0, cbig_ctas = 0;
     int32_t *touched = nullptr;    // [table slots * n] touched entries of the dense wedge tables
     int32_t *mlist = nullptr;      // [n] medium tier sorted by decreasing wedge work
+    int64_t *hub_off = nullptr, *hub_len = nullptr, *hub_pre = nullptr, *hub_scan_tmp = nullptr;
+    int64_t hub_flat_cap = 0;      // hub batch size x largest degree
     int32_t *tlist = nullptr;      // [n] tiny tier (warp per vertex)
     int64_t *west = nullptr;       // [n] wedge work of medium vertices
     int32_t *tcount = nullptr;     // [64]
@@ -192,6 +194,7 @@ cudaError_t run_node_sums(gd_graph *g);                                      // 
 size_t clique_big_bytes(int32_t dm);                                         // per CTA
 cudaError_t run_cycles(gd_graph *g, bool per_edge, const int32_t *counters_host);
 int32_t table_slots(gd_graph *g);
+int32_t hub_batch(gd_graph *g);
 cudaError_t run_complete(gd_graph *g, int derive_cyc);
 cudaError_t max_degree(gd_graph *g, int32_t *out_host);
 int32_t tribuf_warps(int sms);

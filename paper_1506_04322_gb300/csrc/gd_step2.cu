@@ -495,6 +495,9 @@ struct CycleArgs {
     unsigned long long *yacc;    // per-slot 4-cycle credits (per-edge mode)
     unsigned long long *sums;    // u128 sums: X_C4 gets sum_e C4(e) = 4 * 4-cycles (global mode)
     int32_t hub0, nhub;          // hub batch
+    int64_t *hoff;               // [17] row offsets of the batch's hubs in the flat neighbour list
+    int64_t *hlen;               // [flat] wedges contributed by each neighbour
+    int64_t *hpre;               // [flat + 1] exclusive prefix of hlen (hpre[flat] = batch wedges)
 };
 
 __device__ __forceinline__ unsigned long long c2(uint32_t c) { return (unsigned long long)c * (c - 1) / 2; }
@@ -704,8 +707,41 @@ k_cycles_medium(CycleArgs a) {
     }
 }
 
-// Hub tier, phase PH (0 count, 1 credit): every warp of the grid takes groups
-// of 32 neighbours of the hubs hub0 .. hub0+nhub-1; hub h uses table h.
+// Hub tier preparation: offsets of the batch's hub rows in one flat list.
+__global__ void k_hub_offsets(CycleArgs a) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    int64_t o = 0;
+    for (int h = 0; h < a.nhub; h++) {
+        a.hoff[h] = o;
+        const int32_t u = a.hubs[a.hub0 + h];
+        o += a.rp[u + 1] - a.rp[u];
+    }
+    a.hoff[a.nhub] = o;
+}
+
+// Wedges contributed by each neighbour of each hub of the batch: d_v if v
+// ranks below its hub, else 0.
+__global__ void k_hub_lengths(CycleArgs a) {
+    const int64_t total = a.hoff[a.nhub];
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < total; j += (int64_t)gridDim.x * blockDim.x) {
+        int h = 0;
+        while (h + 1 < a.nhub && a.hoff[h + 1] <= j) h++;
+        const int32_t u = a.hubs[a.hub0 + h];
+        const int32_t bu = a.rp[u], du = a.rp[u + 1] - bu;
+        const int32_t i = (int32_t)(j - a.hoff[h]);
+        const int32_t v = a.ci[bu + i], dv = a.nd[bu + i];
+        a.hlen[j] = precedes(dv, v, du, u) ? dv : 0;
+    }
+}
+
+constexpr int64_t HUB_CHUNK = 2048;   // wedges per work unit
+
+// Hub tier, phase PH (0 count, 1 credit): the batch's wedges form one flat
+// space (hub rows concatenated, each neighbour contributing its list); every
+// warp takes chunks of HUB_CHUNK consecutive wedges, finds the first
+// neighbour of its chunk by binary search in the prefix, and walks the
+// neighbours 32 at a time, clipping the lists that straddle the chunk ends.
+// Hub h counts into table h.
 template <int PH>
 __global__ void __launch_bounds__(256)
 k_cycles_hub(CycleArgs a) {
@@ -713,45 +749,75 @@ k_cycles_hub(CycleArgs a) {
     const int lane = lane_id(), warp = threadIdx.x >> 5;
     item[warp][lane] = 0;
     __syncwarp();
-    // units: (hub h, group g of 32 neighbours)
-    int64_t units = 0;
-    for (int h = 0; h < a.nhub; h++) {
-        const int32_t u = a.hubs[a.hub0 + h];
-        units += (a.rp[u + 1] - a.rp[u] + WARP - 1) / WARP;
-    }
+    const int64_t flat = a.hoff[a.nhub];
+    const int64_t wtot = a.hpre[flat];
+    const int64_t units = (wtot + HUB_CHUNK - 1) / HUB_CHUNK;
     for (int64_t unit = global_warp(); unit < units; unit += num_warps()) {
-        int h = 0;
-        int64_t rem = unit;
-        int32_t u = 0, bu = 0, du = 0;
-        for (; h < a.nhub; h++) {
-            u = a.hubs[a.hub0 + h];
-            bu = a.rp[u]; du = a.rp[u + 1] - bu;
-            const int64_t g = (du + WARP - 1) / WARP;
-            if (rem < g) break;
-            rem -= g;
+        const int64_t w_lo = unit * HUB_CHUNK;
+        const int64_t w_hi = min(wtot, w_lo + HUB_CHUNK);
+        // largest j with hpre[j] <= w_lo
+        int64_t lo = 0, hi = flat;
+        while (lo < hi) {
+            const int64_t mid = (lo + hi + 1) >> 1;
+            if (a.hpre[mid] <= w_lo) lo = mid; else hi = mid - 1;
         }
-        uint32_t *tab = a.tables + (int64_t)h * a.n;
-        const int32_t i0 = (int32_t)rem * WARP;
-        const int32_t i1 = min(du, i0 + WARP);
-        if (PH == 0) {
-            warp_wedges(u, du, bu, i0, i1, WARP, a.rp, a.ci, a.nd,
-                [&](int k, int32_t q, int32_t y, bool ok, bool live) {
+        for (int64_t j0 = lo; j0 < flat && a.hpre[j0] < w_hi; j0 += WARP) {
+            // lane l: neighbour j0 + l, its wedges clipped to [w_lo, w_hi)
+            const int64_t j = j0 + lane;
+            int32_t len = 0, start = 0, u = 0, du = 0, slot_uv = -1, h = 0;
+            if (j < flat) {
+                const int64_t p0 = a.hpre[j], p1 = a.hpre[j + 1];
+                const int64_t s0 = max(p0, w_lo), e0 = min(p1, w_hi);
+                if (e0 > s0) {
+                    while (h + 1 < a.nhub && a.hoff[h + 1] <= j) h++;
+                    u = a.hubs[a.hub0 + h];
+                    const int32_t bu = a.rp[u];
+                    du = a.rp[u + 1] - bu;
+                    slot_uv = bu + (int32_t)(j - a.hoff[h]);
+                    const int32_t v = a.ci[slot_uv];
+                    len = (int32_t)(e0 - s0);
+                    start = a.rp[v] + (int32_t)(s0 - p0);
+                }
+            }
+            const int32_t incl = warp_incl_scan(len);
+            const int32_t total = __shfl_sync(FULL, incl, 31);
+            const int32_t excl = incl - len;
+            for (int32_t w0 = 0; w0 < total; w0 += WARP) {
+                const int32_t w = w0 + lane;
+                int32_t k = 0;
+#pragma unroll
+                for (int s = 16; s >= 1; s >>= 1) {
+                    const int32_t e = __shfl_sync(FULL, excl, k + s);
+                    if (e <= w) k += s;
+                }
+                const int32_t ks = __shfl_sync(FULL, start, k);
+                const int32_t ke = __shfl_sync(FULL, excl, k);
+                const int32_t ku = __shfl_sync(FULL, u, k);
+                const int32_t kdu = __shfl_sync(FULL, du, k);
+                const int32_t kh = __shfl_sync(FULL, h, k);
+                const bool live = w < total;
+                bool ok = false;
+                int32_t q = 0, y = 0;
+                if (live) {
+                    q = ks + (w - ke);
+                    y = a.ci[q];
+                    ok = precedes(a.nd[q], y, kdu, ku);
+                }
+                uint32_t *tab = a.tables + (int64_t)kh * a.n;
+                if (PH == 0) {
                     if (ok) atomicAdd(tab + y, 1u);      // result unused: a reduction
-                },
-                [&](int32_t) {});
-        } else {
-            warp_wedges(u, du, bu, i0, i1, WARP, a.rp, a.ci, a.nd,
-                [&](int k, int32_t q, int32_t y, bool ok, bool live) {
+                } else {
                     const uint32_t c = ok ? __ldcg(tab + y) : 0;
                     if (c > 1) atomicAdd(a.yacc + q, (unsigned long long)(c - 1));
                     item_add(item[warp], k, c > 1 ? c - 1 : 0, live);
-                },
-                [&](int32_t it) {
-                    __syncwarp();
-                    const unsigned long long s = item[warp][lane];
-                    if (s) { atomicAdd(a.yacc + bu + it + lane, s); item[warp][lane] = 0; }
-                    __syncwarp();
-                });
+                }
+            }
+            if (PH == 1) {
+                __syncwarp();
+                const unsigned long long s = item[warp][lane];
+                if (s) { atomicAdd(a.yacc + slot_uv, s); item[warp][lane] = 0; }
+                __syncwarp();
+            }
         }
     }
 }
@@ -960,9 +1026,18 @@ cudaError_t run_cycles(gd_graph *g, bool per_edge, const int32_t *cnt) {
     a.hub0 = 0; a.nhub = 0;
     // hubs, in batches
     const int32_t nh = cnt[C_HUB], B = hub_batch(g);
+    a.hoff = w.hub_off; a.hlen = w.hub_len; a.hpre = w.hub_pre;
     for (int32_t h0 = 0; h0 < nh; h0 += B) {
         a.hub0 = h0;
         a.nhub = nh - h0 < B ? nh - h0 : B;
+        GD_LAUNCH(g, "k_hub_offsets", k_hub_offsets, 1, 32, 0, a);
+        // lengths beyond the batch's flat list stay 0, so one scan over the
+        // capacity gives the prefix (and the total at every index >= flat)
+        e = cudaMemsetAsync(w.hub_len, 0, sizeof(int64_t) * (size_t)w.hub_flat_cap, g->stream);
+        if (e) return e;
+        GD_LAUNCH(g, "k_hub_lengths", k_hub_lengths, (unsigned)(sms * 4), 256, 0, a);
+        e = exclusive_scan_i64(g, w.hub_len, w.hub_pre, w.hub_flat_cap, w.hub_scan_tmp);
+        if (e) return e;
         GD_LAUNCH(g, "k_cycles_hub_count", k_cycles_hub<0>, (unsigned)(sms * 8), 256, 0, a);
         if (per_edge) GD_LAUNCH(g, "k_cycles_hub_credit", k_cycles_hub<1>, (unsigned)(sms * 8), 256, 0, a);
         if (per_edge) GD_LAUNCH(g, "k_cycles_hub_clear", k_cycles_hub_clear<true>, (unsigned)(sms * 4), 256, 0, a);
