@@ -58,6 +58,8 @@ def parse():
     ap.add_argument("--global-only", action="store_true", help="time gd_count_global instead")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-graphs measurement")
     ap.add_argument("--no-serving", action="store_true", help="skip the request-loop measurement")
+    ap.add_argument("--workload", default="chung_lu_1m", choices=["chung_lu_1m", "chung_lu_400k"],
+                    help="chung_lu_400k: a 4M-edge graph of the same family, for profiler captures")
     return ap.parse_args()
 
 
@@ -366,7 +368,11 @@ def run_gd(args):
         dist.init_process_group("nccl")
     device = local if ws > 1 else 0
     torch.cuda.set_device(device)
-    g = inputs.chung_lu_1m()
+    if args.workload == "chung_lu_400k":
+        g = inputs.chung_lu(400_000, 2.1, 4_400_000, 20_000.0, 9)
+        g.name = "chung_lu_n400k_gamma2.1_cap20k"
+    else:
+        g = inputs.chung_lu_1m()
     m = g.m
 
     ctx = gd.Context(device, smem_table_max=args.smem_table, bitmap_max_outdeg=args.bitmap_max,

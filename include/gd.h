@@ -116,7 +116,7 @@ typedef struct gd_options {
                                     with a larger out-degree uses pairwise tests
                                     (default and maximum 1024, minimum 2)       */
     int32_t hub_wedges_log2;  /* vertices with more than 2^k wedges are processed
-                                 by the whole GPU in batches (default 21)       */
+                                 by the whole GPU in batches (default 18)       */
     int32_t reserved[6];
 } gd_options;
 

@@ -394,7 +394,7 @@ void gd_default_options(gd_options *opt) {
     opt->ctas_per_sm = 0;
     opt->smem_table_max = 8192;
     opt->bitmap_max_outdeg = gdi::CL_D2;
-    opt->hub_wedges_log2 = 21;
+    opt->hub_wedges_log2 = 18;
 }
 
 static int check_options(gd_options *o) {
@@ -402,7 +402,7 @@ static int check_options(gd_options *o) {
     if (t < 256 || t > 16384 || (t & (t - 1))) return GD_EINVAL;
     if (o->variant < 0 || o->variant > 2) return GD_EINVAL;
     if (o->bitmap_max_outdeg == 0) o->bitmap_max_outdeg = gdi::CL_D2;
-    if (o->hub_wedges_log2 == 0) o->hub_wedges_log2 = 21;
+    if (o->hub_wedges_log2 == 0) o->hub_wedges_log2 = 18;
     if (o->bitmap_max_outdeg < 2 || o->bitmap_max_outdeg > gdi::CL_D2 || o->hub_wedges_log2 < 4 ||
         o->hub_wedges_log2 > 40) return GD_EINVAL;
     return GD_OK;
