@@ -70,6 +70,24 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(x: float, device=None) -> float:
+    """Largest value of x over all ranks (the slowest replica sets the job's
+    time); x itself when no process group is running."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank: int, world: int, seconds: float) -> float:
+    """Whole-job throughput: the units all replicas processed over the
+    slowest replica's time."""
+    return world * units_per_rank / seconds
+
+
 # ---------------------------------------------------------------------------
 # clocks during the timed region
 # ---------------------------------------------------------------------------
@@ -137,31 +155,80 @@ class ClockSampler:
 # algorithmic bytes (per kernel launch) from the CSR
 # ---------------------------------------------------------------------------
 
-def algorithmic_bytes(g) -> dict:
-    """Bytes each kernel's algorithm must move for this graph (4-byte ids,
-    8-byte counters), per launch.  Definitions:
-      step1  = sum_e [4(du+dv) + 32]      both lists of every edge + row bounds
-               (the marking pass of Algorithm 2, Step 1)
-      final  = per edge: 12 B edge list + 8 B slots + 4 B |Tri| + 32 B credits
-               + 24 B A_u/A_v/D_T + 32 B node sums + 16 B row bounds,
-               120 B of per-edge columns written
-      wedge  = sum over oriented wedges (u, v, y), v and y ranked below u, of
-               2 x (4 B id + 8 B row bounds of y) = 24 B per wedge visit
+KERNEL_FAMILIES = {
+    # bitmap passes over N+(a): triangles + 4-cliques, and the triangle sums
+    "bitmap": ("k_clique_bitmap", "k_trisum_bitmap"),
+    # 4-cycle tiers (wedge walks)
+    "cycles": ("k_cycles_tiny", "k_cycles_small", "k_cycles_medium", "k_cycles_hub_count",
+               "k_cycles_hub_credit", "k_cycles_hub_clear"),
+}
+
+
+def algorithmic_bytes(g, triangles: int, per_edge: bool) -> dict:
+    """Bytes each kernel family must move for this graph, per step (4-byte
+    ids, degrees and |Tri| counters, 8-byte credits).  Nodes are ranked by
+    (degree, id); a -> c orients every edge from the lower-ranked end.
+
+    bitmap (one pass for global counts, a second for the per-edge triangle
+      sums): per pass the out-lists N+(a) (12 B per out-edge: id, slot,
+      degree) and the out-lists of their members (4 B per entry,
+      X = sum over out-edges a->c of |N+(c)|); per triangle the (b,c) slot
+      lookup (8 B) and its credits (|Tri| 4 B + 4-clique 8 B in the first
+      pass; three |Tri| reads 12 B + two 8 B credits in the second).
+    cycles (4-cycles counted from their top-ranked node u): every adjacency
+      entry of u read once (id + degree, 8 B each, 16 B per edge); for every
+      lower neighbour v the whole list N(v) scanned (8 B per entry,
+      W = sum over edges of the smaller degree); one counter update per live
+      wedge (y ranked below u; L wedges, 4 B).  The per-edge credit pass
+      repeats the scan, reads each live counter (4 B), credits (v,y) (8 B)
+      and credits each (u,v) once (8 B).
     """
     d = g.degrees().astype(np.int64)
-    e = g.edges()
-    du, dv = d[e[:, 0]], d[e[:, 1]]
-    m = len(e)
-    step1 = int((4 * (du + dv) + 32).sum())
-    wedges = int(np.minimum(du, dv).sum())   # sum_e d(lower-ranked endpoint)
-    return {
-        "k_triangles": step1,
-        "k_tri_sums": step1,
-        "k_final": m * (12 + 8 + 4 + 32 + 24 + 32 + 16 + 120),
-        "k_cycles_wedges": 24 * wedges,
-        "wedges": wedges,
-        "step1": step1,
-    }
+    n = g.n
+    rank = np.empty(n, dtype=np.int64)
+    rank[np.lexsort((np.arange(n), d))] = np.arange(n)
+    rows = np.repeat(np.arange(n, dtype=np.int64), d)
+    cols = g.col_idx.astype(np.int64)
+    m = len(cols) // 2
+    up = rank[cols] > rank[rows]                          # out-edge rows -> cols
+    dplus = np.bincount(rows[up], minlength=n)
+    X = int(dplus[cols[up]].sum())
+    W = int(d[rows[up]].sum())                            # lower end's degree per edge
+    # live wedges: for v and a higher neighbour u, the members of N(v) ranked below u
+    order = np.lexsort((rank[cols], rows))
+    pos = np.empty(len(cols), dtype=np.int64)
+    pos[order] = np.arange(len(cols)) - g.row_ptr[rows[order]]
+    L = int(pos[up].sum())
+    passes = 2 if per_edge else 1
+    bitmap = passes * (12 * m + 4 * X) + triangles * (20 + (36 if per_edge else 0))
+    cycles = 16 * m + 8 * W + 4 * L
+    if per_edge:
+        cycles += 16 * m + 8 * W + 12 * L + 8 * m
+    return {"bitmap": bitmap, "cycles": cycles, "W": W, "L": L, "X": X, "m": m}
+
+
+def source_digest() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1506_04322_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(csrc, f), "rb") as fh:
+                h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(workload: str, family: str):
+    """DRAM bytes per step of a kernel family from the committed ncu summary
+    of this workload, if it was taken on the current kernel sources."""
+    p = os.path.join(ROOT, "profiles", f"traffic_{workload}.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        t = json.load(f)
+    if t.get("source_digest") != source_digest():
+        return None
+    return t.get("families", {}).get(family)
 
 
 def run_batch_measure(gd, torch, ctx, device, steps: int, loop_graphs: int = 600) -> dict:
@@ -426,12 +493,8 @@ def run_gd(args):
         torch.distributed.barrier()
     clk = clocks.stop() if rank == 0 else None
 
-    ms = total_ms / args.steps
-    if ws > 1:
-        t = torch.tensor([ms], device=device, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    value = ws * m / (ms / 1000.0)
+    ms = max_over_ranks(total_ms / args.steps, device)
+    value = job_rate(m, ws, ms / 1000.0)
 
     # end to end through the C ABI with pinned host buffers
     rp_h = torch.from_numpy(g.row_ptr).pin_memory()
@@ -458,33 +521,30 @@ def run_gd(args):
     e2e_s = (time.perf_counter() - t0) / e2e_steps
     if r != glob:
         raise RuntimeError("end-to-end counts differ from the device-resident counts")
-    if ws > 1:
-        t = torch.tensor([e2e_s], device=device, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(e2e_s, device)
 
     if rank != 0:
         if ws > 1:
             torch.distributed.destroy_process_group()
         return
 
-    # roofline of the dominant kernel
-    ab = algorithmic_bytes(g)
+    # roofline of the dominant kernel family (all its launches in a step)
     peak, peak_kind = load_peaks()
     kern = {k: {"ms_per_launch": v[0] / max(v[1], 1), "launches": v[1], "ms_total": v[0]} for k, v in prof.items()}
-    dom = max(kern, key=lambda k: kern[k]["ms_total"])
-    if dom in ab:
-        bytes_per_launch = ab[dom]
-    elif dom.startswith("k_cycles"):
-        bytes_per_launch = ab["k_cycles_wedges"]
-    else:
-        bytes_per_launch = None
-    roof = None
-    if bytes_per_launch:
-        achieved = bytes_per_launch / (kern[dom]["ms_per_launch"] / 1000.0) / 1e9
-        roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
-                "algorithmic_bytes_per_launch": bytes_per_launch}
+    fam_ms = {f: sum(kern[k]["ms_total"] for k in names if k in kern) / args.steps
+              for f, names in KERNEL_FAMILIES.items()}
+    dom = max(fam_ms, key=fam_ms.get)
+    ab = algorithmic_bytes(g, int(glob[0]), not args.global_only)
+    achieved = ab[dom] / (fam_ms[dom] / 1000.0) / 1e9
+    traffic = measured_traffic(g.name, dom)
+    roof = {"kernel": dom, "kernels": [k for k in KERNEL_FAMILIES[dom] if k in kern], "bound": "hbm",
+            "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": traffic, "peak_kind": peak_kind, "algorithmic_bytes_per_step": ab[dom],
+            "ms_per_step": fam_ms[dom], "per": "step (all launches of the family)",
+            "launches_per_step": sum(kern[k]["launches"] for k in KERNEL_FAMILIES[dom] if k in kern) // args.steps,
+            "other_families": {f: {"ms_per_step": fam_ms[f], "algorithmic_bytes_per_step": ab[f],
+                                   "achieved_gbs": ab[f] / (fam_ms[f] / 1000.0) / 1e9 if fam_ms[f] else None}
+                               for f in fam_ms if f != dom}}
 
     batch = None
     if not args.no_batch:
@@ -506,14 +566,18 @@ def run_gd(args):
                    "mode": "global" if args.global_only else "per-edge (15 columns) + global",
                    "variant": "oriented", "seed": 2, "l2": "flushed between timed steps (512 MB write)",
                    "parallelism": f"replicas x{ws}"},
-        "e2e": {"value": ws * m / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "e2e": {"value": job_rate(m, ws, e2e_s), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
+        "launches_before_timed": launches0,
+        "family_launches_per_step": {f: sum(kern[k]["launches"] for k in names if k in kern) // args.steps
+                                     for f, names in KERNEL_FAMILIES.items()},
         "roofline": roof,
         "cpu_baseline": cpu,
         "clocks": clk,
         "batch": batch,
         "serving": serving,
         "kernels": {k: round(v["ms_total"] / args.steps, 3) for k, v in sorted(kern.items(), key=lambda kv: -kv[1]["ms_total"])},
+        "source_digest": source_digest(),
         "global_counts": [str(x) for x in glob],
     }
     print(json.dumps(line), flush=True)
