@@ -242,6 +242,7 @@ size_t estimate_footprint(gd_ctx *ctx, int64_t n, int64_t nnz, bool per_edge, bo
     size_t b = round_block(sizeof(int32_t) * (size_t)(n + 1 + nnz)) + round_block(16);   // CSR + status
     for (const AllocSpec &a : sp) b += round_block(a.bytes);
     if (per_edge && host_out) b += round_block(sizeof(uint64_t) * 15 * (size_t)(nnz / 2));
+    if (n > 0) b += round_block(clique_pairs_bound(ctx ? ctx->num_sms : 152, n));
     g.ws = Workspace();
     return b;
 }
@@ -266,6 +267,21 @@ int ensure_clique_scratch(gd_graph *g, const int32_t *cnt) {
     int rc = dalloc(g, (void **)&w.cbig, need);
     if (rc) return rc;
     w.cbig_bytes = need; w.cbig_stride = stride; w.cbig_dm = dm; w.cbig_ctas = ctas;
+    return GD_OK;
+}
+
+// Per-team triangle records of the clique kernels, sized for this graph's
+// bucket counts.
+int ensure_pairs(gd_graph *g, const int32_t *cnt) {
+    Workspace &w = g->ws;
+    size_t need = 0;
+    GD_CK(g->ctx, clique_pairs_bytes(g, cnt, &need));
+    if (w.pairs && w.pairs_bytes >= need) return GD_OK;
+    if (w.pairs) { release_block(g, w.pairs); w.pairs = nullptr; w.pairs_bytes = 0; }
+    if (need == 0) return GD_OK;
+    int rc = dalloc(g, (void **)&w.pairs, need);
+    if (rc) return rc;
+    w.pairs_bytes = need;
     return GD_OK;
 }
 
@@ -601,6 +617,7 @@ static int count_path(gd_graph *g, bool per_edge, uint64_t *out_dev) {
     GD_CK(ctx, run_schedule(g, cnt));
     if (cnt[C_CL0 + 3] > 0 && (rc = ensure_clique_scratch(g, cnt))) return rc;
     if (cnt[C_HUB] > 0 && (rc = ensure_hub_scratch(g))) return rc;
+    if ((rc = ensure_pairs(g, cnt))) return rc;
     GD_CK(ctx, run_triangles_cliques(g, per_edge, cnt));
     bool cliq_credits = per_edge, qr_credits = false;
     if (per_edge) {

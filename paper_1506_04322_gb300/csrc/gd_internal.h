@@ -46,6 +46,7 @@ enum CounterIdx {
     C_TINY = 9,     // vertices in the warp-level wedge tier
     C_MB0 = 16,     // medium tier: vertices per log2(wedges) bucket (40 buckets)
     C_MOFF = 64,    // medium tier: placement offsets per bucket (40)
+    C_CLD0 = 104,   // clique kernels: work counters (pass x bucket, 8)
     C_NUM = 112
 };
 constexpr int MB_BUCKETS = 40;
@@ -87,6 +88,8 @@ struct Workspace {
     int32_t *dag_off = nullptr;    // [n+1] out-lists under the degree ordering
     int32_t *dag_col = nullptr, *dag_slot = nullptr, *dag_nd = nullptr;   // [m]
     uint32_t *tcred = nullptr;     // [nnz] triangle credits per slot
+    unsigned long long *pairs = nullptr;   // per-team triangle records of the clique kernels
+    size_t pairs_bytes = 0;
     unsigned char *cbig = nullptr; // per-CTA scratch of the large out-list clique kernel
     size_t cbig_bytes = 0, cbig_stride = 0;
     int32_t cbig_dm = 0, cbig_ctas = 0;
@@ -191,7 +194,9 @@ cudaError_t run_schedule(gd_graph *g, int32_t *counters_host);
 cudaError_t run_triangles_cliques(gd_graph *g, bool per_edge, const int32_t *counters_host);
 cudaError_t run_triangle_sums(gd_graph *g, const int32_t *counters_host);   // Q/R credits (needs |Tri|)
 cudaError_t run_node_sums(gd_graph *g);                                      // t(x), S1(x)
-size_t clique_big_bytes(int32_t dm);                                         // per CTA
+size_t clique_big_bytes(int32_t dm);
+cudaError_t clique_pairs_bytes(gd_graph *g, const int32_t *counters_host, size_t *need);
+size_t clique_pairs_bound(int sms, int64_t n);                                         // per CTA
 cudaError_t run_cycles(gd_graph *g, bool per_edge, const int32_t *counters_host);
 int32_t table_slots(gd_graph *g);
 int32_t hub_batch(gd_graph *g);

@@ -9,22 +9,24 @@
 //             out-list has at most sqrt(2|E|) entries.
 //   tiers     vertices by wedge work W(u) = sum_{v in N(u), v below u} d_v.
 //
-// Triangles and 4-cliques ("bitmap" kernels).  For every node a with
-// D = |N+(a)| <= 1024, one CTA builds the adjacency matrix M of the subgraph
-// induced by N+(a) in shared memory, rows and columns in rank order.  For
-// each b in N+(a), S_b = M[b] restricted to ranks above b is Tri+(a,b), the
-// triangles {a, b, c} whose lowest node is a and middle node is b, and every
-// set bit pair {c, d} of S_b joined in M is a 4-clique {a, b, c, d} whose two
-// lowest nodes are a and b.  Each triangle and each 4-clique is therefore
-// found exactly once, and the credits to all its edges are aggregated:
-//   triangle {a,b,c}:  (a,b) += |S_b|, (a,c) += per-c counter, (b,c) += 1
-//   4-clique {a,b,c,d} (a<b<c<d in rank):
-//       (a,b) += |E(S_b)|                           once per (a,b)
-//       (a,c),(a,d) += |M[c] & S_b| summed over b   once per (a,c)
-//       (b,c),(b,d) += |M[c] & S_b|                 once per triangle
-//       (c,d) += |M[c] & M[d] & below(c)|           once per edge inside N+(a)
+// Triangles and 4-cliques ("bitmap" kernels).  For every node a, a team (a
+// warp for |N+(a)| <= 64, a CTA up to 1024, a CTA on global scratch above)
+// walks the pairs (c, x) with c in N+(a) and x in N+(c), the concatenated
+// out-lists spread over the lanes.  A pair whose x is in N+(a) too is the
+// triangle {a, c, x} with a lowest, found exactly once, and the scan holds
+// the CSR slots of all three of its edges:
+//   triangle {a,c,x}:  (c,x) += 1 directly, (a,c) and (a,x) through per-c
+//                      counters flushed once per node
+// The same scan sets the adjacency matrix M of the subgraph induced by
+// N+(a) (shared memory, one bit per pair).  For an edge (c, x) inside
+// N+(a), the common neighbours of c and x in M are the 4-cliques
+// {a, c, x, d} with a lowest; a second scan credits them:
+//   4-clique {a,c,x,d}: (c,x) += |M[c] & M[x]| once per inner edge,
+//                       (a,c) += half the sum over the inner edges at c
 // Per-edge |Tri_e| and cliq_e are the sums of the credits of both slots of
-// the edge.  For the global count only the number of 4-cliques is kept.
+// the edge.  For the global count only sum |M[c] & M[x]| = 3 K4 is kept.
+// The triangle-sum pass needs no matrix: one scan credits each triangle's
+// perimeter and degree sum to its three edges.
 //
 // 4-cycles.  Every 4-cycle is counted once from its highest-ranked node u
 // with opposite node y: cnt[y] = number of v below u adjacent to u and y
@@ -38,6 +40,7 @@
 //   hubs   : a batch of hubs at a time, every CTA of the GPU working on the
 //            same few dense tables (so they stay in L2), one launch per phase.
 #include <cuda_runtime.h>
+#include <algorithm>
 #include <stdint.h>
 
 #include "gd_device.cuh"
@@ -168,24 +171,9 @@ struct CliqueArgs {
     unsigned char *gstore;      // per-CTA work arrays of the large out-list variant
     int32_t gdmax;              // its capacity (multiple of 32, >= largest out-degree)
     size_t gstride;             // bytes per CTA
-};
-
-// Bytes of the large out-list variant's per-CTA work arrays.
-__host__ __device__ inline size_t clique_gstore_bytes(int32_t dm, int threads) {
-    const size_t W = (size_t)dm / 32;
-    return (size_t)dm * 48 + (size_t)dm * W * 4 + (size_t)(threads / 32) * W * 4 + 256;
-}
-
-template <int DMAX>
-struct CliqueSmem {
-    static constexpr int W = DMAX / 32;
-    int32_t ids[DMAX];          // N+(a), ascending ids
-    int32_t degs[DMAX];         // their degrees
-    int32_t rank_of[DMAX];      // rank index of ids[k] within N+(a)
-    int32_t rid[DMAX], rslot[DMAX], rdeg[DMAX];   // by rank index
-    uint32_t cnt_p[DMAX], tri_p[DMAX];
-    unsigned long long qa[DMAX], ra[DMAX];         // triangle-sum mode
-    uint32_t M[DMAX * W];       // adjacency, row r = node of rank index r
+    int32_t *dyn;               // work counter of this launch (zero at launch)
+    unsigned long long *pairs;  // per-team triangle records (COUNT, CREDIT)
+    int32_t pair_cap;           // records per team (0: none)
 };
 
 // MODE_COUNT: |Tri| credits + number of 4-cliques (global counts)
@@ -196,185 +184,346 @@ struct CliqueSmem {
 //   Q(e) = A_u + A_v + T(e)^2 and R(e) = D_T + T(e)(d_u + d_v).
 enum { MODE_COUNT = 0, MODE_CREDIT = 1, MODE_TRISUM = 2 };
 
-// binary search of id `key` in the out-list of node x; returns the CSR slot
-// of the edge (x, key) or -1
-__device__ __forceinline__ int32_t out_slot(const CliqueArgs &a, int32_t x, int32_t key) {
-    const int32_t o = a.dag_off[x], d = a.dag_off[x + 1] - o;
-    int32_t lo = 0, hi = d;
-    while (lo < hi) { const int32_t mid = (lo + hi) >> 1; if (ldg(a.dag_col + o + mid) < key) lo = mid + 1; else hi = mid; }
-    if (lo >= d || ldg(a.dag_col + o + lo) != key) return -1;
-    return ldg(a.dag_slot + o + lo);
+// Open-addressing table of N+(a) (id -> position), at least twice as many
+// slots as entries, and a one-bit filter over the same ids (about 32 bits
+// per entry) that rejects most non-members with one shared-memory load.
+__host__ __device__ constexpr int32_t clique_hash_slots(int32_t D) {
+    int32_t s = 32;
+    while (s < 2 * D) s <<= 1;
+    return s;
+}
+__host__ __device__ constexpr int clique_filter_bits(int32_t D) {
+    int b = 11;
+    while ((1ll << b) < 32ll * D) b++;
+    return b;
+}
+__device__ __forceinline__ uint32_t clique_hash(int32_t x, int bits) {
+    return ((uint32_t)x * 0x9E3779B1u) >> (32 - bits);
 }
 
-// Work arrays of one CTA: in shared memory (DMAX > 0) or in the CTA's slice
-// of global scratch (DMAX == 0: out-lists above the shared-memory limit).
+constexpr int CQ = 64;   // candidate queue entries per warp
+
+// Work arrays of one team (a warp or a CTA working on one node a), for an
+// out-list of at most D entries (D a multiple of 32).  Position k is the
+// k-th entry of N+(a) (ascending ids).
 struct CliqueView {
-    int32_t *ids, *degs, *rank_of, *rid, *rslot, *rdeg;
-    uint32_t *cnt_p, *tri_p;
-    unsigned long long *qa, *ra;
-    uint32_t *M, *Sbuf;
+    unsigned long long *qa, *ra;   // TRISUM: P and R credits of (a, c_k)
+    int32_t *aslot;                // CSR slot of (a, c_k)
+    uint32_t *acc;                 // TRISUM: |Tri| of (a, c_k); else triangles on (a, c_k)
+    int32_t *st;                   // DAG offset of N+(c_k)
+    int32_t *pre;                  // exclusive prefix of |N+(c_k)|, pre[D] = total
+    int32_t *hkey;                 // hash keys (ids, -1 empty)
+    uint32_t *filt;                // membership filter
+    int32_t *qx, *qq;              // candidate queues (per warp: CQ entries)
+    int32_t *adeg;                 // TRISUM: d(c_k)
+    uint32_t *cnt;                 // CREDIT: twice the 4-cliques on (a, c_k)
+    uint32_t *M;                   // COUNT/CREDIT: adjacency inside N+(a), D/32 words a row
+    uint16_t *hpos;                // hash values (positions)
+    uint16_t *qk;                  // candidate queue: list position
 };
 
-template <int DMAX, int THREADS, int MODE>
+template <int MODE>
+__host__ __device__ constexpr size_t team_bytes(int32_t D, int warps) {
+    return (MODE == MODE_TRISUM ? (size_t)D * 16 : 0)          // qa, ra
+           + (size_t)D * 12 + (size_t)(D + 32) * 4              // aslot, acc, st, pre
+           + (size_t)clique_hash_slots(D) * 4                   // hkey
+           + ((size_t)1 << clique_filter_bits(D)) / 8           // filt
+           + (size_t)warps * CQ * 8                             // qx, qq
+           + (MODE != MODE_COUNT ? (size_t)D * 4 : 0)           // adeg or cnt
+           + (MODE != MODE_TRISUM ? (size_t)D * (size_t)(D / 32) * 4 : 0)   // M
+           + (size_t)clique_hash_slots(D) * 2                   // hpos
+           + (size_t)warps * CQ * 2;                            // qk
+}
+
+template <int MODE>
+__device__ __forceinline__ CliqueView carve(unsigned char *base, int32_t D, int warps) {
+    CliqueView S;
+    S.qa = S.ra = nullptr;
+    if (MODE == MODE_TRISUM) {
+        S.qa = reinterpret_cast<unsigned long long *>(base);
+        S.ra = S.qa + D;
+        base += (size_t)D * 16;
+    }
+    int32_t *p = reinterpret_cast<int32_t *>(base);
+    S.aslot = p; p += D;
+    S.acc = reinterpret_cast<uint32_t *>(p); p += D;
+    S.st = p; p += D;
+    S.pre = p; p += D + 32;
+    S.hkey = p; p += clique_hash_slots(D);
+    S.filt = reinterpret_cast<uint32_t *>(p); p += (1 << clique_filter_bits(D)) / 32;
+    S.qx = p; p += warps * CQ;
+    S.qq = p; p += warps * CQ;
+    S.adeg = p;
+    S.cnt = reinterpret_cast<uint32_t *>(p);
+    if (MODE != MODE_COUNT) p += D;
+    S.M = reinterpret_cast<uint32_t *>(p);
+    if (MODE != MODE_TRISUM) p += (size_t)D * (D / 32);
+    S.hpos = reinterpret_cast<uint16_t *>(p);
+    S.qk = S.hpos + clique_hash_slots(D);
+    return S;
+}
+
+// Position of id x in N+(a), or -1.
+__device__ __forceinline__ int32_t clique_find(const CliqueView &S, int32_t x, int bits) {
+    const uint32_t mask = (1u << bits) - 1u;
+    uint32_t h = clique_hash(x, bits);
+    for (uint32_t probe = 0; probe <= mask; probe++) {
+        const int32_t k = S.hkey[h];
+        if (k == x) return S.hpos[h];
+        if (k < 0) return -1;
+        h = (h + 1) & mask;
+    }
+    return -1;
+}
+
+// Every pair (c, x) with c in N+(a) and x in N+(c): the concatenated
+// out-lists (total pre[D]) are split into 32-entry groups, each warp of the
+// team taking a contiguous share of the groups; a lane finds the list of its
+// entry by walking forward from the list of the previous group's last entry
+// (no walk when the group lies inside one list).  Entries that pass the
+// filter go to the warp's queue; 32 at a time, the lanes look them up in the
+// table and call f(kc, kx, q) for every pair whose x is in N+(a) too: kc, kx
+// are the positions of c and x in N+(a), q the DAG entry of x in N+(c), so
+// dag_slot[q] is the CSR slot of (c, x).  Each such pair is the triangle
+// {a, c, x} with a lowest, found exactly once.
+template <int TW, typename F>
+__device__ __forceinline__ void scan_pairs(const CliqueArgs &a, const CliqueView &S, int32_t D, int bits, int fbits,
+                                           int tw, F f) {
+    const int lane = lane_id();
+    const unsigned lt = (1u << lane) - 1u;
+    int32_t *qx = S.qx + tw * CQ, *qq = S.qq + tw * CQ;
+    uint16_t *qk = S.qk + tw * CQ;
+    auto drain = [&](int32_t cnt) {
+        __syncwarp();
+        if (lane < cnt) {
+            const int32_t kx = clique_find(S, qx[lane], bits);
+            if (kx >= 0) f((int32_t)qk[lane], kx, qq[lane]);
+        }
+        __syncwarp();
+    };
+    const int32_t total = S.pre[D];
+    const int32_t G = (total + 31) >> 5;
+    const int32_t g0 = (int32_t)(((int64_t)G * tw) / TW), g1 = (int32_t)(((int64_t)G * (tw + 1)) / TW);
+    if (g0 >= g1) return;
+    // list of the first entry: the last k with pre[k] <= g0 * 32
+    int32_t lo = 0, hi = D - 1;
+    {
+        const int32_t w0 = g0 * 32;
+        while (lo < hi) {
+            const int32_t mid = (lo + hi + 1) >> 1;
+            if (S.pre[mid] <= w0) lo = mid; else hi = mid - 1;
+        }
+    }
+    int32_t kcur = lo, qn = 0;
+    for (int32_t g = g0; g < g1; g++) {
+        const int32_t w0 = g * 32, w = w0 + lane;
+        int32_t k = kcur;
+        bool cand = false;
+        int32_t x = 0, q = 0;
+        if (w < total) {
+            if (S.pre[kcur + 1] < w0 + 32)
+                while (S.pre[k + 1] <= w) k++;
+            q = S.st[k] + (w - S.pre[k]);
+            x = ldg(a.dag_col + q);
+            const uint32_t fh = clique_hash(x, fbits);
+            cand = (S.filt[fh >> 5] >> (fh & 31)) & 1u;
+        }
+        const unsigned m = __ballot_sync(FULL, cand);
+        if (cand) {
+            const int32_t p = qn + __popc(m & lt);
+            qx[p] = x; qq[p] = q; qk[p] = (uint16_t)k;
+        }
+        qn += __popc(m);
+        if (qn >= 32) {
+            drain(32);
+            if (lane < qn - 32) { qx[lane] = qx[32 + lane]; qq[lane] = qq[32 + lane]; qk[lane] = qk[32 + lane]; }
+            qn -= 32;
+            __syncwarp();
+        }
+        kcur = __shfl_sync(FULL, k, 31);
+    }
+    if (qn > 0) drain(qn);
+}
+
+// One team per node a of the bucket, the nodes taken in list order from a
+// shared counter.  WARP_TEAMS: every warp of the CTA is a team with its own
+// slice of shared memory (small out-lists); otherwise the whole CTA is one
+// team.  DMAX == 0: work arrays in the CTA's slice of global scratch
+// (out-lists above the shared-memory limit).  COUNT and CREDIT record the
+// triangles found by the first scan (positions and the slot of (c, x)) in the
+// team's slice of a.pairs, so the 4-clique phase walks only those; a node
+// with more than a.pair_cap of them scans its lists again instead.
+template <int DMAX, int THREADS, bool WARP_TEAMS, int MODE>
 __global__ void __launch_bounds__(THREADS)
 k_clique_bitmap(CliqueArgs a) {
     constexpr int NW = THREADS / 32;
+    constexpr int TEAMS = WARP_TEAMS ? NW : 1;
+    constexpr int TW = WARP_TEAMS ? 1 : NW;          // warps per team
+    static_assert(DMAX > 0 || !WARP_TEAMS, "global scratch holds one team per CTA");
     extern __shared__ __align__(16) unsigned char smraw[];
-    CliqueView S;
-    int W;
-    if (DMAX > 0) {
-        CliqueSmem<(DMAX > 0 ? DMAX : 32)> &Sm = *reinterpret_cast<CliqueSmem<(DMAX > 0 ? DMAX : 32)> *>(smraw);
-        S.ids = Sm.ids; S.degs = Sm.degs; S.rank_of = Sm.rank_of; S.rid = Sm.rid; S.rslot = Sm.rslot;
-        S.rdeg = Sm.rdeg; S.cnt_p = Sm.cnt_p; S.tri_p = Sm.tri_p; S.qa = Sm.qa; S.ra = Sm.ra; S.M = Sm.M;
-        S.Sbuf = reinterpret_cast<uint32_t *>(smraw + sizeof(CliqueSmem<(DMAX > 0 ? DMAX : 32)>));
-        W = DMAX / 32;
-    } else {
-        const int32_t dm = a.gdmax;
-        unsigned char *base = a.gstore + (size_t)blockIdx.x * a.gstride;
-        S.qa = (unsigned long long *)base;
-        S.ra = S.qa + dm;
-        int32_t *p = (int32_t *)(S.ra + dm);
-        S.ids = p; S.degs = p + dm; S.rank_of = p + 2 * dm; S.rid = p + 3 * dm; S.rslot = p + 4 * dm;
-        S.rdeg = p + 5 * dm;
-        S.cnt_p = (uint32_t *)(p + 6 * dm); S.tri_p = S.cnt_p + dm;
-        S.M = S.tri_p + dm;
-        W = dm / 32;
-        S.Sbuf = S.M + (size_t)dm * W;
-    }
+    __shared__ int32_t wsum[NW];
+    __shared__ int32_t next_idx;
     const int lane = lane_id(), warp = threadIdx.x >> 5;
+    const int team = WARP_TEAMS ? warp : 0;
+    const int tw = WARP_TEAMS ? 0 : warp;            // warp index inside the team
+    const int tt = tw * 32 + lane;                   // thread index inside the team
+    const int32_t dm = DMAX > 0 ? DMAX : a.gdmax;
+    unsigned char *base = DMAX > 0 ? smraw + (size_t)team * team_bytes<MODE>(DMAX, TW)
+                                   : a.gstore + (size_t)blockIdx.x * a.gstride;
+    const CliqueView S = carve<MODE>(base, dm, TW);
+    int32_t *npair = S.pre + dm + 16;                // triangles recorded for the current node
+    unsigned long long *mypairs = a.pairs + ((size_t)blockIdx.x * TEAMS + team) * (size_t)a.pair_cap;
+    auto team_sync = [] { if (WARP_TEAMS) __syncwarp(); else __syncthreads(); };
+    // next node index of this team (the counter hands out list positions)
+    auto take = [&](int32_t mine) {
+        if (WARP_TEAMS) return __shfl_sync(FULL, mine, 0);
+        if (threadIdx.x == 0) next_idx = mine;
+        __syncthreads();
+        const int32_t v = next_idx;
+        __syncthreads();
+        return v;
+    };
+
     const int32_t nv = a.counters[C_CL0 + a.bucket];
     const int32_t *list = a.clist + (int64_t)a.bucket * a.n;
-    unsigned long long k4_local = 0;
-    uint32_t *mys = S.Sbuf + warp * W;
+    unsigned long long k4_local = 0;   // 3 x 4-cliques (COUNT)
 
-    for (int32_t idx = blockIdx.x; idx < nv; idx += gridDim.x) {
+    int32_t idx = take(tt == 0 ? atomicAdd(a.dyn, 1) : 0);
+    while (idx < nv) {
+        const int32_t pending = tt == 0 ? atomicAdd(a.dyn, 1) : 0;   // the team's next node
         const int32_t va = list[idx];
         const int32_t off = a.dag_off[va], D = a.dag_off[va + 1] - off;
-        const int Wd = (D + 31) >> 5;
-        for (int k = threadIdx.x; k < D; k += THREADS) { S.ids[k] = a.dag_col[off + k]; S.degs[k] = a.dag_nd[off + k]; }
-        for (int k = threadIdx.x; k < D * Wd; k += THREADS) S.M[k] = 0;
-        for (int k = threadIdx.x; k < D; k += THREADS) {
-            if (MODE == MODE_TRISUM) { S.qa[k] = 0; S.ra[k] = 0; }
-            else { S.cnt_p[k] = 0; S.tri_p[k] = 0; }
-        }
-        __syncthreads();
-        // rank index of each out-neighbour (number of out-neighbours below it)
-        for (int k = threadIdx.x; k < D; k += THREADS) {
-            const int32_t dk = S.degs[k], ik = S.ids[k];
-            int32_t r = 0;
-            for (int j = 0; j < D; j++) r += precedes(S.degs[j], S.ids[j], dk, ik);
-            S.rank_of[k] = r;
-            S.rid[r] = ik; S.rslot[r] = a.dag_slot[off + k]; S.rdeg[r] = dk;
-        }
-        __syncthreads();
-        // adjacency inside N+(a): for c in N+(a), every x in N+(c) that is in N+(a)
-        for (int k = warp; k < D; k += NW) {
-            const int32_t c = S.ids[k], rc = S.rank_of[k];
-            const int32_t co = a.dag_off[c], cd = a.dag_off[c + 1] - co;
-            for (int32_t t = lane; t < cd; t += WARP) {
-                const int32_t x = a.dag_col[co + t];
-                int32_t lo = 0, hi = D;
-                while (lo < hi) { const int32_t mid = (lo + hi) >> 1; if (S.ids[mid] < x) lo = mid + 1; else hi = mid; }
-                if (lo < D && S.ids[lo] == x) {
-                    const int32_t rx = S.rank_of[lo];
-                    atomicOr(&S.M[rc * Wd + (rx >> 5)], 1u << (rx & 31));
-                    atomicOr(&S.M[rx * Wd + (rc >> 5)], 1u << (rc & 31));
-                }
-            }
-        }
-        __syncthreads();
-        const int32_t da = a.rp[va + 1] - a.rp[va];
-        // for each b (rank index rb): S_b = M[rb] & ranks above rb
-        for (int rb = warp; rb < D; rb += NW) {
-            uint32_t nS = 0;
-            for (int w = lane; w < Wd; w += WARP) {
-                uint32_t x = S.M[rb * Wd + w];
-                const int lo = rb + 1;   // keep ranks >= lo
-                if (w * 32 + 31 < lo) x = 0;
-                else if (w * 32 < lo) x &= ~((1u << (lo - w * 32)) - 1u);
-                mys[w] = x;
-                nS += __popc(x);
-            }
-            nS = warp_sum(nS);
-            __syncwarp();
-            if (nS == 0) continue;
-            const int32_t b = S.rid[rb];
+        const int32_t Wd = (D + 31) >> 5;
+        const int32_t hs = clique_hash_slots(D);
+        const int bits = 31 - __clz(hs);
+        const int fbits = clique_filter_bits(D);
+        for (int32_t i = tt; i < hs; i += TW * 32) S.hkey[i] = -1;
+        for (int32_t i = tt; i < (1 << fbits) / 32; i += TW * 32) S.filt[i] = 0;
+        if (MODE != MODE_TRISUM)
+            for (int32_t i = tt; i < D * Wd; i += TW * 32) S.M[i] = 0;
+        if (tt == 0) *npair = 0;
+        team_sync();
+        for (int32_t k = tt; k < D; k += TW * 32) {
+            const int32_t c = ldg(a.dag_col + off + k);
+            const int32_t s = ldg(a.dag_slot + off + k);
+            const int32_t o = ldg(a.dag_off + c);
+            S.aslot[k] = s;
+            S.st[k] = o;
+            S.pre[k] = ldg(a.dag_off + c + 1) - o;
             if (MODE == MODE_TRISUM) {
-                const unsigned long long tab = a.tslot[S.rslot[rb]];
-                const unsigned long long dsum_ab = (unsigned long long)da + S.rdeg[rb];
-                unsigned long long qsum = 0, rsum = 0;
-                for (int q = rb + 1 + lane; q < D; q += WARP) {
-                    if (!((mys[q >> 5] >> (q & 31)) & 1u)) continue;
-                    const int32_t sbc = out_slot(a, b, S.rid[q]);
-                    if (sbc < 0) { atomicOr(a.status, ERR_CAPACITY); continue; }
-                    const unsigned long long P = tab + a.tslot[S.rslot[q]] + a.tslot[sbc];
-                    const unsigned long long R = dsum_ab + S.rdeg[q];
-                    qsum += P; rsum += R;
-                    atomicAdd(&S.qa[q], P);
-                    atomicAdd(&S.ra[q], R);
-                    atomicAdd(a.qcred + sbc, P);
-                    atomicAdd(a.rcred + sbc, R);
-                }
-                qsum = warp_sum(qsum);
-                rsum = warp_sum(rsum);
-                if (lane == 0) {
-                    atomicAdd(a.qcred + S.rslot[rb], qsum);
-                    atomicAdd(a.rcred + S.rslot[rb], rsum);
-                }
-                __syncwarp();
-                continue;
-            }
-            unsigned long long k2 = 0;   // ordered adjacent pairs inside S_b
-            for (int q = rb + 1 + lane; q < D; q += WARP) {
-                if (!((mys[q >> 5] >> (q & 31)) & 1u)) continue;
-                uint32_t kq = 0;
-                for (int w = 0; w < Wd; w++) kq += __popc(S.M[q * Wd + w] & mys[w]);
-                k2 += kq;
-                atomicAdd(&S.tri_p[q], 1u);
-                if (MODE == MODE_CREDIT) atomicAdd(&S.cnt_p[q], kq);
-                // slot of (b, c_q): c_q is in N+(b)
-                const int32_t sbc = out_slot(a, b, S.rid[q]);
-                if (sbc < 0) { atomicOr(a.status, ERR_CAPACITY); continue; }
-                atomicAdd(a.tcred + sbc, 1u);
-                if (MODE == MODE_CREDIT && kq) atomicAdd(a.cacc + sbc, (unsigned long long)kq);
-            }
-            k2 = warp_sum(k2);
-            if (lane == 0) {
-                atomicAdd(a.tcred + S.rslot[rb], nS);
-                if (MODE == MODE_CREDIT && k2) atomicAdd(a.cacc + S.rslot[rb], k2 >> 1);
-                k4_local += k2 >> 1;
-            }
-            __syncwarp();
-        }
-        __syncthreads();
-        // per-node credits of (a, c) and pair credits of edges (c, d) inside N+(a)
-        for (int q = threadIdx.x; q < D; q += THREADS) {
-            if (MODE == MODE_TRISUM) {
-                if (S.qa[q]) atomicAdd(a.qcred + S.rslot[q], S.qa[q]);
-                if (S.ra[q]) atomicAdd(a.rcred + S.rslot[q], S.ra[q]);
+                S.adeg[k] = ldg(a.dag_nd + off + k);
+                S.acc[k] = __ldg(a.tslot + s);
+                S.qa[k] = 0;
+                S.ra[k] = 0;
             } else {
-                if (S.tri_p[q]) atomicAdd(a.tcred + S.rslot[q], S.tri_p[q]);
-                if (MODE == MODE_CREDIT && S.cnt_p[q]) atomicAdd(a.cacc + S.rslot[q], (unsigned long long)S.cnt_p[q]);
+                S.acc[k] = 0;
+                if (MODE == MODE_CREDIT) S.cnt[k] = 0;
             }
+            // the table has at least 2D slots, so a free one is always found
+            uint32_t h = clique_hash(c, bits);
+            int32_t probe = 0;
+            for (; probe < hs; probe++) {
+                if (atomicCAS(&S.hkey[h], -1, c) == -1) { S.hpos[h] = (uint16_t)k; break; }
+                h = (h + 1) & (uint32_t)(hs - 1);
+            }
+            if (probe == hs) atomicOr(a.status, ERR_CAPACITY);
+            const uint32_t fh = clique_hash(c, fbits);
+            atomicOr(&S.filt[fh >> 5], 1u << (fh & 31));
         }
-        if (MODE == MODE_CREDIT) {
-            for (int p = warp; p < D; p += NW) {
-                const int32_t cp = S.rid[p];
-                const int pw = p >> 5;
-                for (int q = p + 1 + lane; q < D; q += WARP) {
-                    if (!((S.M[p * Wd + (q >> 5)] >> (q & 31)) & 1u)) continue;
-                    uint32_t pc = 0;
-                    for (int w = 0; w < pw; w++) pc += __popc(S.M[p * Wd + w] & S.M[q * Wd + w]);
-                    if (p & 31) pc += __popc(S.M[p * Wd + pw] & S.M[q * Wd + pw] & ((1u << (p & 31)) - 1u));
-                    if (!pc) continue;
-                    // c_p ranks below c_q, so c_q is in N+(c_p)
-                    const int32_t scd = out_slot(a, cp, S.rid[q]);
-                    if (scd < 0) { atomicOr(a.status, ERR_CAPACITY); continue; }
-                    atomicAdd(a.cacc + scd, (unsigned long long)pc);
+        team_sync();
+        // pre <- exclusive prefix of the list lengths
+        {
+            int32_t carry = 0;
+            for (int32_t r0 = 0; r0 < D; r0 += TW * 32) {
+                const int32_t k = r0 + tt;
+                const int32_t v = k < D ? S.pre[k] : 0;
+                const int32_t incl = warp_incl_scan(v);
+                if (TW > 1) {
+                    if (lane == 31) wsum[tw] = incl;
+                    __syncthreads();
+                    int32_t before = 0, all = 0;
+                    for (int j = 0; j < TW; j++) { const int32_t s = wsum[j]; before += j < tw ? s : 0; all += s; }
+                    __syncthreads();
+                    if (k < D) S.pre[k] = carry + before + incl - v;
+                    carry += all;
+                } else {
+                    if (k < D) S.pre[k] = carry + incl - v;
+                    carry += __shfl_sync(FULL, incl, 31);
                 }
             }
+            if (tt == 0) S.pre[D] = carry;
         }
-        __syncthreads();
+        team_sync();
+
+        if (MODE == MODE_TRISUM) {
+            const unsigned long long da = (unsigned long long)(a.rp[va + 1] - a.rp[va]);
+            scan_pairs<TW>(a, S, D, bits, fbits, tw, [&](int32_t kc, int32_t kx, int32_t q) {
+                const int32_t s = ldg(a.dag_slot + q);
+                const unsigned long long P = (unsigned long long)S.acc[kc] + S.acc[kx] + __ldg(a.tslot + s);
+                const unsigned long long R = da + (unsigned long long)S.adeg[kc] + (unsigned long long)S.adeg[kx];
+                atomicAdd(a.qcred + s, P);
+                atomicAdd(a.rcred + s, R);
+                atomicAdd(&S.qa[kc], P);
+                atomicAdd(&S.qa[kx], P);
+                atomicAdd(&S.ra[kc], R);
+                atomicAdd(&S.ra[kx], R);
+            });
+            team_sync();
+            for (int32_t k = tt; k < D; k += TW * 32) {
+                if (S.qa[k]) atomicAdd(a.qcred + S.aslot[k], S.qa[k]);
+                if (S.ra[k]) atomicAdd(a.rcred + S.aslot[k], S.ra[k]);
+            }
+        } else {
+            // adjacency inside N+(a), the triangle credits, the triangle record
+            scan_pairs<TW>(a, S, D, bits, fbits, tw, [&](int32_t kc, int32_t kx, int32_t q) {
+                const int32_t s = ldg(a.dag_slot + q);
+                atomicOr(&S.M[kc * Wd + (kx >> 5)], 1u << (kx & 31));
+                atomicOr(&S.M[kx * Wd + (kc >> 5)], 1u << (kc & 31));
+                atomicAdd(a.tcred + s, 1u);
+                atomicAdd(&S.acc[kc], 1u);
+                atomicAdd(&S.acc[kx], 1u);
+                const int32_t i = atomicAdd(npair, 1);
+                if (i < a.pair_cap)
+                    mypairs[i] = ((unsigned long long)(uint32_t)s << 32) | ((uint32_t)kx << 16) | (uint32_t)kc;
+            });
+            team_sync();
+            const int32_t np = *npair;
+            // inner edge (c, x): the 4-cliques {a, c, x, d} are the common
+            // neighbours d of c and x inside N+(a)
+            auto inner = [&](int32_t kc, int32_t kx, int32_t s) {
+                uint32_t kq = 0;
+                for (int32_t w = 0; w < Wd; w++) kq += __popc(S.M[kc * Wd + w] & S.M[kx * Wd + w]);
+                if (MODE == MODE_COUNT) {
+                    k4_local += kq;
+                } else if (kq) {
+                    atomicAdd(a.cacc + s, (unsigned long long)kq);
+                    atomicAdd(&S.cnt[kc], kq);
+                    atomicAdd(&S.cnt[kx], kq);
+                }
+            };
+            if (np <= a.pair_cap) {
+                for (int32_t i = tt; i < np; i += TW * 32) {
+                    const unsigned long long v = mypairs[i];
+                    inner((int32_t)(v & 0xffffu), (int32_t)((v >> 16) & 0xffffu), (int32_t)(v >> 32));
+                }
+            } else if (MODE == MODE_CREDIT) {
+                scan_pairs<TW>(a, S, D, bits, fbits, tw, [&](int32_t kc, int32_t kx, int32_t q) {
+                    inner(kc, kx, ldg(a.dag_slot + q));
+                });
+            } else {
+                for (int32_t kc = tw; kc < D; kc += TW)
+                    for (int32_t kx = kc + 1 + lane; kx < D; kx += WARP)
+                        if ((S.M[kc * Wd + (kx >> 5)] >> (kx & 31)) & 1u) inner(kc, kx, 0);
+            }
+            team_sync();
+            // credits of the edges (a, c_k)
+            for (int32_t k = tt; k < D; k += TW * 32) {
+                if (S.acc[k]) atomicAdd(a.tcred + S.aslot[k], S.acc[k]);
+                if (MODE == MODE_CREDIT && S.cnt[k]) atomicAdd(a.cacc + S.aslot[k], (unsigned long long)(S.cnt[k] >> 1));
+            }
+        }
+        team_sync();
+        idx = take(pending);
     }
     if (MODE == MODE_COUNT) {
         __shared__ unsigned long long red[NW];
@@ -384,7 +533,8 @@ k_clique_bitmap(CliqueArgs a) {
         if (threadIdx.x == 0) {
             unsigned long long s = 0;
             for (int w = 0; w < NW; w++) s += red[w];
-            add_u128(a.sums + 2 * S_CLIQ, 6ull * s);   // sum_e cliq_e = 6 f41
+            if (s % 3 != 0) atomicOr(a.status, ERR_REMAINDER);
+            add_u128(a.sums + 2 * S_CLIQ, 2ull * s);   // sum_e cliq_e = 6 K4 = 2 (3 K4)
         }
     }
 }
@@ -915,12 +1065,34 @@ cudaError_t run_schedule(gd_graph *g, int32_t *counters_host) {
     return cudaGetLastError();
 }
 
-size_t clique_smem_bytes(int dmax, int threads) {
-    const int W = dmax / 32;
-    return (size_t)dmax * 4 * 7 + (size_t)dmax * W * 4 + (size_t)(threads / 32) * W * 4 + 64;
+// Triangle records per team: a warp team (out-degree <= 64) never holds more
+// than C(64, 2); larger teams fall back to a second scan past 8192.
+constexpr int32_t PAIR_CAP_WARP = CL_D0 * (CL_D0 - 1) / 2;
+constexpr int32_t PAIR_CAP_CTA = 8192;
+
+template <int DMAX, int THREADS, bool WARP_TEAMS, int MODE>
+static cudaError_t clique_grid(gd_graph *g, int count, unsigned *grid, size_t *smem_out) {
+    constexpr int TEAMS = WARP_TEAMS ? THREADS / 32 : 1;
+    const size_t smem = DMAX > 0 ? (size_t)TEAMS * team_bytes<MODE>(DMAX, WARP_TEAMS ? 1 : THREADS / 32) : 0;
+    auto kern = k_clique_bitmap<DMAX, THREADS, WARP_TEAMS, MODE>;
+    *smem_out = smem;
+    if (DMAX == 0) {
+        *grid = (unsigned)g->ws.cbig_ctas;     // the global scratch holds this many CTAs
+        return cudaSuccess;
+    }
+    cudaError_t e = allow_smem(kern, smem);
+    if (e) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, THREADS, smem);
+    if (e) return e;
+    *grid = grid_for((count + TEAMS - 1) / TEAMS, 1, sms_of(g) * (per_sm > 0 ? per_sm : 1));
+    return cudaSuccess;
 }
 
-template <int DMAX, int THREADS, int MODE>
+template <int DMAX, int THREADS, bool WARP_TEAMS>
+static constexpr int32_t pair_cap_of() { return DMAX == 0 ? 0 : WARP_TEAMS ? PAIR_CAP_WARP : PAIR_CAP_CTA; }
+
+template <int DMAX, int THREADS, bool WARP_TEAMS, int MODE>
 static cudaError_t launch_clique(gd_graph *g, int bucket, int count) {
     if (count == 0) return cudaSuccess;
     Workspace &w = g->ws;
@@ -931,35 +1103,66 @@ static cudaError_t launch_clique(gd_graph *g, int bucket, int count) {
     a.qcred = (unsigned long long *)w.qcred; a.rcred = (unsigned long long *)w.rcred;
     a.sums = w.sums; a.status = w.status;
     a.gstore = w.cbig; a.gdmax = w.cbig_dm; a.gstride = w.cbig_stride;
-    const size_t smem = DMAX > 0 ? sizeof(CliqueSmem<(DMAX > 0 ? DMAX : 32)>) + (size_t)(THREADS / 32) * (DMAX / 32) * 4 : 0;
-    cudaError_t e;
+    a.dyn = w.counters + C_CLD0 + (MODE == MODE_TRISUM ? 4 : 0) + bucket;
+    constexpr int TEAMS = WARP_TEAMS ? THREADS / 32 : 1;
     unsigned grid;
-    if (DMAX > 0) {
-        e = allow_smem(k_clique_bitmap<DMAX, THREADS, MODE>, smem);
-        if (e) return e;
-        int per_sm = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_clique_bitmap<DMAX, THREADS, MODE>, THREADS, smem);
-        if (e) return e;
-        grid = grid_for(count, 1, sms_of(g) * (per_sm > 0 ? per_sm : 1));
-    } else {
-        grid = (unsigned)w.cbig_ctas;     // the global scratch holds this many CTAs
-        if (grid == 0) return cudaErrorInvalidValue;
-    }
+    size_t smem;
+    cudaError_t e = clique_grid<DMAX, THREADS, WARP_TEAMS, MODE>(g, count, &grid, &smem);
+    if (e) return e;
+    if (grid == 0) return cudaErrorInvalidValue;
+    a.pairs = w.pairs;
+    a.pair_cap = MODE == MODE_TRISUM ? 0 : pair_cap_of<DMAX, THREADS, WARP_TEAMS>();
+    if ((size_t)grid * TEAMS * (size_t)a.pair_cap * 8 > w.pairs_bytes) a.pair_cap = 0;
     const char *name = MODE == MODE_TRISUM ? "k_trisum_bitmap" : "k_clique_bitmap";
-    GD_LAUNCH(g, name, (k_clique_bitmap<DMAX, THREADS, MODE>), grid, THREADS, smem, a);
+    GD_LAUNCH(g, name, (k_clique_bitmap<DMAX, THREADS, WARP_TEAMS, MODE>), grid, THREADS, smem, a);
     return cudaGetLastError();
 }
 
 template <int MODE>
 static cudaError_t launch_clique_buckets(gd_graph *g, const int32_t *cnt) {
     cudaError_t e;
-    if ((e = launch_clique<CL_D0, 32, MODE>(g, 0, cnt[C_CL0]))) return e;
-    if ((e = launch_clique<CL_D1, 128, MODE>(g, 1, cnt[C_CL0 + 1]))) return e;
-    if ((e = launch_clique<CL_D2, 512, MODE>(g, 2, cnt[C_CL0 + 2]))) return e;
-    return launch_clique<0, CL_BIG_THREADS, MODE>(g, 3, cnt[C_CL0 + 3]);
+    if ((e = launch_clique<CL_D0, 256, true, MODE>(g, 0, cnt[C_CL0]))) return e;
+    if ((e = launch_clique<CL_D1, 256, false, MODE>(g, 1, cnt[C_CL0 + 1]))) return e;
+    if ((e = launch_clique<CL_D2, 512, false, MODE>(g, 2, cnt[C_CL0 + 2]))) return e;
+    return launch_clique<0, CL_BIG_THREADS, false, MODE>(g, 3, cnt[C_CL0 + 3]);
 }
 
-size_t clique_big_bytes(int32_t dm) { return clique_gstore_bytes(dm, CL_BIG_THREADS); }
+template <int DMAX, int THREADS, bool WARP_TEAMS>
+static cudaError_t pairs_need(gd_graph *g, int count, size_t *need) {
+    if (count == 0) return cudaSuccess;
+    constexpr int TEAMS = WARP_TEAMS ? THREADS / 32 : 1;
+    for (int mode = 0; mode < 2; mode++) {
+        unsigned grid = 0;
+        size_t smem;
+        cudaError_t e = mode == 0 ? clique_grid<DMAX, THREADS, WARP_TEAMS, MODE_COUNT>(g, count, &grid, &smem)
+                                  : clique_grid<DMAX, THREADS, WARP_TEAMS, MODE_CREDIT>(g, count, &grid, &smem);
+        if (e) return e;
+        const size_t b = (size_t)grid * TEAMS * (size_t)pair_cap_of<DMAX, THREADS, WARP_TEAMS>() * 8;
+        if (b > *need) *need = b;
+    }
+    return cudaSuccess;
+}
+
+// Bytes of triangle records the clique kernels use for these bucket sizes.
+cudaError_t clique_pairs_bytes(gd_graph *g, const int32_t *cnt, size_t *need) {
+    *need = 0;
+    cudaError_t e;
+    if ((e = pairs_need<CL_D0, 256, true>(g, cnt[C_CL0], need))) return e;
+    if ((e = pairs_need<CL_D1, 256, false>(g, cnt[C_CL0 + 1], need))) return e;
+    return pairs_need<CL_D2, 512, false>(g, cnt[C_CL0 + 2], need);
+}
+
+// Upper bound of the same for a graph of n nodes (admission estimates).
+size_t clique_pairs_bound(int sms, int64_t n) {
+    const int64_t b0 = std::min<int64_t>((n + 7) / 8, (int64_t)sms * 8) * 8 * PAIR_CAP_WARP;
+    const int64_t b1 = std::min<int64_t>(n, (int64_t)sms * 8) * PAIR_CAP_CTA;
+    return (size_t)std::max(b0, b1) * 8;
+}
+
+size_t clique_big_bytes(int32_t dm) {
+    const size_t c = team_bytes<MODE_CREDIT>(dm, CL_BIG_THREADS / 32), t = team_bytes<MODE_TRISUM>(dm, CL_BIG_THREADS / 32);
+    return c > t ? c : t;
+}
 
 // Triangles per slot and 4-cliques (credits when per_edge).  Requires the
 // largest out-degree <= bitmap limit (checked by the caller).
