@@ -181,8 +181,9 @@ void workspace_specs(Workspace &w, int64_t n, int64_t m, int64_t nnz, int32_t sl
         out.push_back(spec(&w.s1, n));
         out.push_back(spec(&w.au, m));
         out.push_back(spec(&w.dt, m));
-        out.push_back(spec(&w.qcred, nnz));
-        out.push_back(spec(&w.rcred, nnz));
+        out.push_back(spec(&w.qcred, 2 * nnz));     // (Q, R) credit pair per slot
+        out.push_back(spec(&w.toff, n + 1));
+        out.push_back(spec(&w.tcnt, n));
     }
 }
 
@@ -243,6 +244,7 @@ size_t estimate_footprint(gd_ctx *ctx, int64_t n, int64_t nnz, bool per_edge, bo
     for (const AllocSpec &a : sp) b += round_block(a.bytes);
     if (per_edge && host_out) b += round_block(sizeof(uint64_t) * 15 * (size_t)(nnz / 2));
     if (n > 0) b += round_block(clique_pairs_bound(ctx ? ctx->num_sms : 152, n));
+    if (per_edge) b += round_block(sizeof(unsigned long long) * 2 * (size_t)nnz);   // triangle records (typical)
     g.ws = Workspace();
     return b;
 }
@@ -282,6 +284,25 @@ int ensure_pairs(gd_graph *g, const int32_t *cnt) {
     int rc = dalloc(g, (void **)&w.pairs, need);
     if (rc) return rc;
     w.pairs_bytes = need;
+    return GD_OK;
+}
+
+// Triangle records kept from the 4-clique pass for the triangle-sum pass
+// (per-edge mode): up to `total` entries, capped at 16 bytes per CSR slot
+// plus 1 GB; nodes past the cap scan again.  A failed allocation only
+// disables the records.
+int ensure_records(gd_graph *g, int64_t total) {
+    Workspace &w = g->ws;
+    const int64_t cap = std::min<int64_t>(total, 2 * g->nnz + (int64_t(1) << 27));
+    if (w.recs && w.recs_cap >= cap) return GD_OK;
+    if (w.recs) { release_block(g, w.recs); w.recs = nullptr; w.recs_cap = 0; }
+    if (cap <= 0) return GD_OK;
+    if (dalloc(g, (void **)&w.recs, sizeof(unsigned long long) * (size_t)cap) != GD_OK) {
+        w.recs = nullptr;
+        g->ctx->err.clear();
+        return GD_OK;
+    }
+    w.recs_cap = cap;
     return GD_OK;
 }
 
@@ -618,6 +639,11 @@ static int count_path(gd_graph *g, bool per_edge, uint64_t *out_dev) {
     if (cnt[C_CL0 + 3] > 0 && (rc = ensure_clique_scratch(g, cnt))) return rc;
     if (cnt[C_HUB] > 0 && (rc = ensure_hub_scratch(g))) return rc;
     if ((rc = ensure_pairs(g, cnt))) return rc;
+    if (per_edge) {
+        int64_t total = 0;
+        GD_CK(ctx, run_tri_bound(g, &total));
+        if ((rc = ensure_records(g, total))) return rc;
+    }
     GD_CK(ctx, run_triangles_cliques(g, per_edge, cnt));
     bool cliq_credits = per_edge, qr_credits = false;
     if (per_edge) {

@@ -310,7 +310,7 @@ struct FinalArgs {
     const int32_t *rp, *eu, *ev, *eslot, *mate;
     const uint32_t *tslot;
     const uint64_t *tnode, *s1, *au, *dt;        // au: A_u + A_v per edge
-    const unsigned long long *qcred, *rcred;     // triangle-perimeter / degree-sum credits per slot
+    const unsigned long long *qcred;             // per slot: triangle-perimeter credit, then degree-sum credit
     int qr_credits;                              // A_u + A_v and D_T from the credits
     const unsigned long long *cacc, *yacc;
     uint64_t *out;
@@ -367,8 +367,8 @@ __global__ void k_final(FinalArgs a) {
         int64_t A, DT;
         if (a.qr_credits) {
             const int32_t q = a.mate[p];
-            A = (int64_t)(a.qcred[p] + a.qcred[q]) - T * T;
-            DT = (int64_t)(a.rcred[p] + a.rcred[q]) - T * (du + dv);
+            A = (int64_t)(a.qcred[2 * (int64_t)p] + a.qcred[2 * (int64_t)q]) - T * T;
+            DT = (int64_t)(a.qcred[2 * (int64_t)p + 1] + a.qcred[2 * (int64_t)q + 1]) - T * (du + dv);
         } else {
             A = (int64_t)a.au[k];
             DT = (int64_t)a.dt[k];
@@ -618,7 +618,7 @@ cudaError_t run_final(gd_graph *g, int variant, bool per_edge, bool cliq_credits
     a.cliq_credits = cliq_credits ? 1 : 0;
     a.rp = g->rp; a.eu = w.eu; a.ev = w.ev; a.eslot = w.eslot; a.mate = w.mate; a.tslot = w.tslot;
     a.tnode = w.tnode; a.s1 = w.s1; a.au = w.au; a.dt = w.dt;
-    a.qcred = (const unsigned long long *)w.qcred; a.rcred = (const unsigned long long *)w.rcred;
+    a.qcred = (const unsigned long long *)w.qcred;
     a.qr_credits = qr_credits ? 1 : 0;
     a.cacc = (const unsigned long long *)w.cacc; a.yacc = (const unsigned long long *)w.yacc;
     a.out = out_dev; a.sums = w.sums; a.status = w.status;

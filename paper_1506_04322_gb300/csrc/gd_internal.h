@@ -76,7 +76,7 @@ struct Workspace {
     uint64_t *tnode = nullptr;     // [n] edges inside N(x)
     uint64_t *s1 = nullptr;        // [n] sum of neighbour degrees
     uint64_t *au = nullptr, *dt = nullptr;   // [m] A_u + A_v and D_T (intersection path)
-    uint64_t *qcred = nullptr, *rcred = nullptr;   // [nnz] triangle perimeter / degree-sum credits
+    uint64_t *qcred = nullptr;   // [2 nnz] per slot: triangle-perimeter credit, degree-sum credit
     uint64_t *cacc = nullptr;      // [nnz] 4-clique credits per slot
     uint64_t *yacc = nullptr;      // [nnz] 4-cycle credits per slot (or cyc_e for literal)
     // schedule
@@ -90,6 +90,10 @@ struct Workspace {
     uint32_t *tcred = nullptr;     // [nnz] triangle credits per slot
     unsigned long long *pairs = nullptr;   // per-team triangle records of the clique kernels
     size_t pairs_bytes = 0;
+    int64_t *toff = nullptr;               // per-edge mode: per-node triangle record offsets (n + 1)
+    int32_t *tcnt = nullptr;               // records kept per node, -1 none
+    unsigned long long *recs = nullptr;    // triangle records kept for the triangle-sum pass
+    int64_t recs_cap = 0;                  // entries
     unsigned char *cbig = nullptr; // per-CTA scratch of the large out-list clique kernel
     size_t cbig_bytes = 0, cbig_stride = 0;
     int32_t cbig_dm = 0, cbig_ctas = 0;
@@ -196,6 +200,7 @@ cudaError_t run_triangle_sums(gd_graph *g, const int32_t *counters_host);   // Q
 cudaError_t run_node_sums(gd_graph *g);                                      // t(x), S1(x)
 size_t clique_big_bytes(int32_t dm);
 cudaError_t clique_pairs_bytes(gd_graph *g, const int32_t *counters_host, size_t *need);
+cudaError_t run_tri_bound(gd_graph *g, int64_t *total);
 size_t clique_pairs_bound(int sms, int64_t n);                                         // per CTA
 cudaError_t run_cycles(gd_graph *g, bool per_edge, const int32_t *counters_host);
 int32_t table_slots(gd_graph *g);

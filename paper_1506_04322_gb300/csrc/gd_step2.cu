@@ -164,8 +164,7 @@ struct CliqueArgs {
     unsigned long long *cacc;   // per-slot clique credits (per-edge mode)
     uint32_t *tcred;            // per-slot triangle credits
     const uint32_t *tslot;      // |Tri| per slot (triangle-sum mode)
-    unsigned long long *qcred;  // per-slot triangle-perimeter credits (triangle-sum mode)
-    unsigned long long *rcred;  // per-slot triangle degree-sum credits (triangle-sum mode)
+    unsigned long long *qcred;  // per slot: triangle-perimeter credit, then degree-sum credit (triangle-sum mode)
     unsigned long long *sums;   // u128 sums (S_CLIQ gets 6 * K4 in global mode)
     int32_t *status;            // error bits
     unsigned char *gstore;      // per-CTA work arrays of the large out-list variant
@@ -174,6 +173,13 @@ struct CliqueArgs {
     int32_t *dyn;               // work counter of this launch (zero at launch)
     unsigned long long *pairs;  // per-team triangle records (COUNT, CREDIT)
     int32_t pair_cap;           // records per team (0: none)
+    // per-edge mode: triangle records kept from the CREDIT pass for the
+    // TRISUM pass, node a's in recs[toff[a], toff[a+1]) when toff[a+1] <=
+    // rec_cap; tcnt[a] = records written, or -1 when a has no region
+    const int64_t *toff;
+    int32_t *tcnt;
+    unsigned long long *recs;
+    int64_t rec_cap;
 };
 
 // MODE_COUNT: |Tri| credits + number of 4-cliques (global counts)
@@ -397,8 +403,13 @@ k_clique_bitmap(CliqueArgs a) {
         const int32_t hs = clique_hash_slots(D);
         const int bits = 31 - __clz(hs);
         const int fbits = clique_filter_bits(D);
-        for (int32_t i = tt; i < hs; i += TW * 32) S.hkey[i] = -1;
-        for (int32_t i = tt; i < (1 << fbits) / 32; i += TW * 32) S.filt[i] = 0;
+        // TRISUM: records kept by the CREDIT pass replace the scan
+        const int32_t ne = (MODE == MODE_TRISUM && a.tcnt != nullptr) ? a.tcnt[va] : -1;
+        const bool scan = ne < 0;
+        if (scan) {
+            for (int32_t i = tt; i < hs; i += TW * 32) S.hkey[i] = -1;
+            for (int32_t i = tt; i < (1 << fbits) / 32; i += TW * 32) S.filt[i] = 0;
+        }
         if (MODE != MODE_TRISUM)
             for (int32_t i = tt; i < D * Wd; i += TW * 32) S.M[i] = 0;
         if (tt == 0) *npair = 0;
@@ -406,10 +417,7 @@ k_clique_bitmap(CliqueArgs a) {
         for (int32_t k = tt; k < D; k += TW * 32) {
             const int32_t c = ldg(a.dag_col + off + k);
             const int32_t s = ldg(a.dag_slot + off + k);
-            const int32_t o = ldg(a.dag_off + c);
             S.aslot[k] = s;
-            S.st[k] = o;
-            S.pre[k] = ldg(a.dag_off + c + 1) - o;
             if (MODE == MODE_TRISUM) {
                 S.adeg[k] = ldg(a.dag_nd + off + k);
                 S.acc[k] = __ldg(a.tslot + s);
@@ -419,6 +427,10 @@ k_clique_bitmap(CliqueArgs a) {
                 S.acc[k] = 0;
                 if (MODE == MODE_CREDIT) S.cnt[k] = 0;
             }
+            if (!scan) continue;
+            const int32_t o = ldg(a.dag_off + c);
+            S.st[k] = o;
+            S.pre[k] = ldg(a.dag_off + c + 1) - o;
             // the table has at least 2D slots, so a free one is always found
             uint32_t h = clique_hash(c, bits);
             int32_t probe = 0;
@@ -432,7 +444,7 @@ k_clique_bitmap(CliqueArgs a) {
         }
         team_sync();
         // pre <- exclusive prefix of the list lengths
-        {
+        if (scan) {
             int32_t carry = 0;
             for (int32_t r0 = 0; r0 < D; r0 += TW * 32) {
                 const int32_t k = r0 + tt;
@@ -457,23 +469,42 @@ k_clique_bitmap(CliqueArgs a) {
 
         if (MODE == MODE_TRISUM) {
             const unsigned long long da = (unsigned long long)(a.rp[va + 1] - a.rp[va]);
-            scan_pairs<TW>(a, S, D, bits, fbits, tw, [&](int32_t kc, int32_t kx, int32_t q) {
-                const int32_t s = ldg(a.dag_slot + q);
+            auto tri = [&](int32_t kc, int32_t kx, int32_t s) {
                 const unsigned long long P = (unsigned long long)S.acc[kc] + S.acc[kx] + __ldg(a.tslot + s);
                 const unsigned long long R = da + (unsigned long long)S.adeg[kc] + (unsigned long long)S.adeg[kx];
-                atomicAdd(a.qcred + s, P);
-                atomicAdd(a.rcred + s, R);
+                atomicAdd(a.qcred + 2 * (int64_t)s, P);
+                atomicAdd(a.qcred + 2 * (int64_t)s + 1, R);
                 atomicAdd(&S.qa[kc], P);
                 atomicAdd(&S.qa[kx], P);
                 atomicAdd(&S.ra[kc], R);
                 atomicAdd(&S.ra[kx], R);
-            });
+            };
+            if (scan) {
+                scan_pairs<TW>(a, S, D, bits, fbits, tw, [&](int32_t kc, int32_t kx, int32_t q) {
+                    tri(kc, kx, ldg(a.dag_slot + q));
+                });
+            } else {
+                const unsigned long long *rec = a.recs + a.toff[va];
+                for (int32_t i = tt; i < ne; i += TW * 32) {
+                    const unsigned long long v = rec[i];
+                    tri((int32_t)(v & 0xffffu), (int32_t)((v >> 16) & 0xffffu), (int32_t)(v >> 32));
+                }
+            }
             team_sync();
             for (int32_t k = tt; k < D; k += TW * 32) {
-                if (S.qa[k]) atomicAdd(a.qcred + S.aslot[k], S.qa[k]);
-                if (S.ra[k]) atomicAdd(a.rcred + S.aslot[k], S.ra[k]);
+                if (S.qa[k]) atomicAdd(a.qcred + 2 * (int64_t)S.aslot[k], S.qa[k]);
+                if (S.ra[k]) atomicAdd(a.qcred + 2 * (int64_t)S.aslot[k] + 1, S.ra[k]);
             }
         } else {
+            // the triangle record: node a's own region when it has one (kept
+            // for the TRISUM pass), else the team's scratch slice
+            unsigned long long *rec = mypairs;
+            int64_t rcap = a.pair_cap;
+            bool stored = false;
+            if (MODE == MODE_CREDIT && a.recs != nullptr) {
+                const int64_t o0 = a.toff[va], o1 = a.toff[va + 1];
+                if (o1 <= a.rec_cap) { rec = a.recs + o0; rcap = o1 - o0; stored = true; }
+            }
             // adjacency inside N+(a), the triangle credits, the triangle record
             scan_pairs<TW>(a, S, D, bits, fbits, tw, [&](int32_t kc, int32_t kx, int32_t q) {
                 const int32_t s = ldg(a.dag_slot + q);
@@ -483,11 +514,16 @@ k_clique_bitmap(CliqueArgs a) {
                 atomicAdd(&S.acc[kc], 1u);
                 atomicAdd(&S.acc[kx], 1u);
                 const int32_t i = atomicAdd(npair, 1);
-                if (i < a.pair_cap)
-                    mypairs[i] = ((unsigned long long)(uint32_t)s << 32) | ((uint32_t)kx << 16) | (uint32_t)kc;
+                if (i < rcap)
+                    rec[i] = ((unsigned long long)(uint32_t)s << 32) | ((uint32_t)kx << 16) | (uint32_t)kc;
             });
             team_sync();
             const int32_t np = *npair;
+            if (MODE == MODE_CREDIT && a.tcnt != nullptr && tt == 0) {
+                // a region holds at most min(C(D,2), pairs scanned) >= np records
+                if (stored && np > rcap) atomicOr(a.status, ERR_CAPACITY);
+                a.tcnt[va] = stored && np <= rcap ? np : -1;
+            }
             // inner edge (c, x): the 4-cliques {a, c, x, d} are the common
             // neighbours d of c and x inside N+(a)
             auto inner = [&](int32_t kc, int32_t kx, int32_t s) {
@@ -501,9 +537,9 @@ k_clique_bitmap(CliqueArgs a) {
                     atomicAdd(&S.cnt[kx], kq);
                 }
             };
-            if (np <= a.pair_cap) {
+            if (np <= rcap) {
                 for (int32_t i = tt; i < np; i += TW * 32) {
-                    const unsigned long long v = mypairs[i];
+                    const unsigned long long v = rec[i];
                     inner((int32_t)(v & 0xffffu), (int32_t)((v >> 16) & 0xffffu), (int32_t)(v >> 32));
                 }
             } else if (MODE == MODE_CREDIT) {
@@ -536,6 +572,23 @@ k_clique_bitmap(CliqueArgs a) {
             if (s % 3 != 0) atomicOr(a.status, ERR_REMAINDER);
             add_u128(a.sums + 2 * S_CLIQ, 2ull * s);   // sum_e cliq_e = 6 K4 = 2 (3 K4)
         }
+    }
+}
+
+// Upper bound of the triangles whose lowest node is a: C(|N+(a)|, 2), and
+// the number of pairs (c, x) a scan of N+(a) visits.
+__global__ void k_tri_bound(int32_t n, const int32_t *__restrict__ dag_off, const int32_t *__restrict__ dag_col,
+                            int64_t *bound) {
+    const int lane = lane_id();
+    for (int32_t u = global_warp(); u < n; u += num_warps()) {
+        const int32_t o = dag_off[u], D = dag_off[u + 1] - o;
+        int64_t x = 0;
+        for (int32_t k = lane; k < D; k += WARP) {
+            const int32_t c = dag_col[o + k];
+            x += dag_off[c + 1] - dag_off[c];
+        }
+        x = warp_sum(x);
+        if (lane == 0) bound[u] = D >= 2 ? min((int64_t)D * (D - 1) / 2, x) : 0;
     }
 }
 
@@ -1100,10 +1153,12 @@ static cudaError_t launch_clique(gd_graph *g, int bucket, int count) {
     a.clist = w.clist; a.counters = w.counters; a.bucket = bucket; a.n = g->n; a.rp = g->rp;
     a.dag_off = w.dag_off; a.dag_col = w.dag_col; a.dag_slot = w.dag_slot; a.dag_nd = w.dag_nd;
     a.cacc = (unsigned long long *)w.cacc; a.tcred = w.tcred; a.tslot = w.tslot;
-    a.qcred = (unsigned long long *)w.qcred; a.rcred = (unsigned long long *)w.rcred;
+    a.qcred = (unsigned long long *)w.qcred;
     a.sums = w.sums; a.status = w.status;
     a.gstore = w.cbig; a.gdmax = w.cbig_dm; a.gstride = w.cbig_stride;
     a.dyn = w.counters + C_CLD0 + (MODE == MODE_TRISUM ? 4 : 0) + bucket;
+    a.toff = w.toff; a.tcnt = w.recs ? w.tcnt : nullptr; a.recs = w.recs; a.rec_cap = w.recs_cap;
+    if (MODE == MODE_COUNT) { a.tcnt = nullptr; a.recs = nullptr; a.rec_cap = 0; }
     constexpr int TEAMS = WARP_TEAMS ? THREADS / 32 : 1;
     unsigned grid;
     size_t smem;
@@ -1152,6 +1207,22 @@ cudaError_t clique_pairs_bytes(gd_graph *g, const int32_t *cnt, size_t *need) {
     return pairs_need<CL_D2, 512, false>(g, cnt[C_CL0 + 2], need);
 }
 
+// Offsets of the per-node triangle record regions (toff, n + 1 entries);
+// *total receives toff[n].
+cudaError_t run_tri_bound(gd_graph *g, int64_t *total) {
+    Workspace &w = g->ws;
+    const int32_t n = g->n;
+    *total = 0;
+    if (n == 0) return cudaSuccess;
+    GD_LAUNCH(g, "k_tri_bound", k_tri_bound, grid_for((int64_t)n * 32, 256, sms_of(g) * 16), 256, 0,
+              n, w.dag_off, w.dag_col, w.scan_tmp);
+    cudaError_t e = exclusive_scan_i64(g, w.scan_tmp, w.toff, n, w.scan_tmp + (n + 1));
+    if (e) return e;
+    e = cudaMemcpyAsync(total, w.toff + n, sizeof(int64_t), cudaMemcpyDeviceToHost, g->stream);
+    if (e) return e;
+    return cudaStreamSynchronize(g->stream);
+}
+
 // Upper bound of the same for a graph of n nodes (admission estimates).
 size_t clique_pairs_bound(int sms, int64_t n) {
     const int64_t b0 = std::min<int64_t>((n + 7) / 8, (int64_t)sms * 8) * 8 * PAIR_CAP_WARP;
@@ -1188,9 +1259,7 @@ cudaError_t run_triangles_cliques(gd_graph *g, bool per_edge, const int32_t *cnt
 cudaError_t run_triangle_sums(gd_graph *g, const int32_t *cnt) {
     Workspace &w = g->ws;
     if (g->m == 0) return cudaSuccess;
-    cudaError_t e = cudaMemsetAsync(w.qcred, 0, sizeof(uint64_t) * g->nnz, g->stream);
-    if (e) return e;
-    e = cudaMemsetAsync(w.rcred, 0, sizeof(uint64_t) * g->nnz, g->stream);
+    cudaError_t e = cudaMemsetAsync(w.qcred, 0, 2 * sizeof(uint64_t) * g->nnz, g->stream);
     if (e) return e;
     return launch_clique_buckets<MODE_TRISUM>(g, cnt);
 }
