@@ -111,12 +111,14 @@ typedef struct gd_options {
                                  (power of two in [256, 16384], default 8192);
                                  vertices with at most half as many wedges use it */
     int32_t bitmap_max_outdeg;   /* nodes with at most this many higher-ranked
-                                    neighbours get the shared-memory adjacency
-                                    (bitmap) triangle/4-clique kernel; a graph
-                                    with a larger out-degree uses pairwise tests
+                                    neighbours keep the triangle/4-clique work
+                                    arrays in shared memory; nodes with more use
+                                    the same kernel on global scratch
                                     (default and maximum 1024, minimum 2)       */
     int32_t hub_wedges_log2;  /* vertices with more than 2^k wedges are processed
-                                 by the whole GPU in batches (default 18)       */
+                                 by the whole GPU in batches; below, one CTA per
+                                 vertex with a table of up to 2^(k+1) entries
+                                 (default 18)                                   */
     int32_t reserved[6];
 } gd_options;
 

@@ -169,13 +169,11 @@ void workspace_specs(Workspace &w, int64_t n, int64_t m, int64_t nnz, int32_t sl
         out.push_back(spec(&w.scan_tmp, 3 * (n + 1) + 4096));
         out.push_back(spec(&w.cacc, nnz));
         out.push_back(spec(&w.yacc, nnz));
-        out.push_back(spec(&w.tcount, 64));
         out.push_back(spec(&w.mlist, n));
-        out.push_back(spec(&w.west, n));
+        out.push_back(spec(&w.west, n + 1));
         out.push_back(spec(&w.tlist, n));
     } else if (part == 1) {
         out.push_back(spec(&w.wtab, (int64_t)slots * n));
-        out.push_back(spec(&w.touched, (int64_t)slots * n));
     } else {
         out.push_back(spec(&w.tnode, n));
         out.push_back(spec(&w.s1, n));
@@ -303,6 +301,25 @@ int ensure_records(gd_graph *g, int64_t total) {
         return GD_OK;
     }
     w.recs_cap = cap;
+    return GD_OK;
+}
+
+// Per-CTA tables of the medium tier: a power of two >= 2 W entries for the
+// largest medium vertex, one per CTA (two per SM, fewer when there are fewer
+// vertices or the tables would pass 8 GB), all entries empty (all ones).
+int ensure_medium_scratch(gd_graph *g, const int32_t *cnt) {
+    Workspace &w = g->ws;
+    int64_t cap = 1024;
+    while (cap < 2 * w.medium_wmax) cap <<= 1;
+    int64_t ctas = std::min<int64_t>(2 * g->ctx->num_sms, cnt[C_MEDIUM]);
+    while (ctas > 1 && ctas * cap * 8 > (int64_t(8) << 30)) ctas /= 2;
+    if (w.mtab && w.mtab_cap >= cap && w.mtab_ctas >= ctas) return GD_OK;
+    if (w.mtab) { release_block(g, w.mtab); w.mtab = nullptr; w.mtab_cap = 0; w.mtab_ctas = 0; }
+    int rc = dalloc(g, (void **)&w.mtab, sizeof(unsigned long long) * (size_t)(ctas * cap));
+    if (rc) return rc;
+    GD_CK(g->ctx, cudaMemsetAsync(w.mtab, 0xff, sizeof(unsigned long long) * (size_t)(ctas * cap), g->stream));
+    w.mtab_cap = cap;
+    w.mtab_ctas = (int32_t)ctas;
     return GD_OK;
 }
 
@@ -638,6 +655,7 @@ static int count_path(gd_graph *g, bool per_edge, uint64_t *out_dev) {
     GD_CK(ctx, run_schedule(g, cnt));
     if (cnt[C_CL0 + 3] > 0 && (rc = ensure_clique_scratch(g, cnt))) return rc;
     if (cnt[C_HUB] > 0 && (rc = ensure_hub_scratch(g))) return rc;
+    if (cnt[C_MEDIUM] > 0 && (rc = ensure_medium_scratch(g, cnt))) return rc;
     if ((rc = ensure_pairs(g, cnt))) return rc;
     if (per_edge) {
         int64_t total = 0;
@@ -927,7 +945,7 @@ int gd_autotune(gd_graph *g, int per_edge, int32_t max_trials, gd_tune_result *r
     int32_t trials = 1;
     const int32_t smem_c[] = {4096, 8192, 16384};
     const int32_t bitmap_c[] = {256, 1024};
-    const int32_t hub_c[] = {18, 21, 24, 40};
+    const int32_t hub_c[] = {14, 16, 18, 20};
     for (int32_t sm : smem_c)
         for (int32_t bm : bitmap_c)
             for (int32_t hb : hub_c) {

@@ -97,17 +97,19 @@ struct Workspace {
     unsigned char *cbig = nullptr; // per-CTA scratch of the large out-list clique kernel
     size_t cbig_bytes = 0, cbig_stride = 0;
     int32_t cbig_dm = 0, cbig_ctas = 0;
-    int32_t *touched = nullptr;    // [table slots * n] touched entries of the dense wedge tables
     int32_t *mlist = nullptr;      // [n] medium tier sorted by decreasing wedge work
     int64_t *hub_off = nullptr, *hub_len = nullptr, *hub_pre = nullptr, *hub_scan_tmp = nullptr;
     int64_t hub_flat_cap = 0;      // hub batch size x largest degree
     int32_t *tlist = nullptr;      // [n] tiny tier (warp per vertex)
     int64_t *west = nullptr;       // [n] wedge work of medium vertices
-    int32_t *tcount = nullptr;     // [64]
     // scratch
     int32_t *tribuf = nullptr;     // [warps * tricap * 3]
     int64_t tribuf_words = 0;
-    uint32_t *wtab = nullptr;      // [big_ctas * n] dense wedge tables (zero at rest)
+    uint32_t *wtab = nullptr;      // [hub batch * n] dense wedge tables (zero at rest)
+    unsigned long long *mtab = nullptr;   // medium tier: per-CTA open-addressing tables (empty at rest)
+    int64_t mtab_cap = 0;                 // entries per CTA (power of two)
+    int32_t mtab_ctas = 0;
+    int64_t medium_wmax = 0;              // largest medium-tier W of the last schedule (host copy)
     int32_t wtab_ctas = 0;
     // results
     unsigned long long *sums = nullptr;   // [2*(S_NUM+X_NUM)] u128 as lo,hi

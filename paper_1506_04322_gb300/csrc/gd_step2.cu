@@ -90,6 +90,7 @@ __global__ void k_schedule(int32_t n, const int32_t *__restrict__ rp, const int3
                 else if (est <= small_cap) vlist[atomicAdd(counters + C_SMALL, 1)] = u;
                 else if (est <= hub_min) {
                     vlist[n - 1 - atomicAdd(counters + C_MEDIUM, 1)] = u;
+                    atomicMax(reinterpret_cast<unsigned long long *>(west + n), (unsigned long long)est);
                     west[u] = est;
                     atomicAdd(counters + C_MB0 + min(MB_BUCKETS - 1, 63 - __clzll(est)), 1);
                 }
@@ -692,11 +693,13 @@ struct CycleArgs {
     const int32_t *vlist, *hubs, *mlist, *tlist;
     int32_t *counters;           // counters[C_DYN] is the medium tier's work index
     uint32_t capmask;
-    uint32_t *tables;            // [slots][n] dense counters, zero at rest
-    int32_t *touched;            // [slots][n]
-    int32_t *tcount;             // [slots]
+    uint32_t *tables;            // [hub batch][n] dense counters, zero at rest
+    unsigned long long *mtab;    // medium tier: per-CTA open-addressing tables, empty at rest
+    int64_t mcap;                // their entries per CTA (power of two)
+    const int64_t *west;         // wedges per medium vertex
     unsigned long long *yacc;    // per-slot 4-cycle credits (per-edge mode)
     unsigned long long *sums;    // u128 sums: X_C4 gets sum_e C4(e) = 4 * 4-cycles (global mode)
+    int32_t *status;             // error bits
     int32_t hub0, nhub;          // hub batch
     int64_t *hoff;               // [17] row offsets of the batch's hubs in the flat neighbour list
     int64_t *hlen;               // [flat] wedges contributed by each neighbour
@@ -846,64 +849,186 @@ k_cycles_small(CycleArgs a) {
     }
 }
 
-// Medium tier: one vertex per CTA at a time, dense global table per CTA.
+// Medium tier: one vertex per CTA at a time.  Its counters live in the
+// CTA's own open-addressing table in global memory, sized to the vertex (a
+// power of two >= 2 W(u), so every insertion finds a slot), which keeps the
+// tables of all CTAs together small enough for L2; the table is reset after
+// each vertex.  An entry is (y << 32) | count, all ones when empty.
+constexpr unsigned long long MH_EMPTY = ~0ull;
+constexpr unsigned long long MH_KEY = 0xffffffff00000000ull;
+
+// cnt[y] += 1; returns the previous count (0xffffffff: table full)
+__device__ __forceinline__ uint32_t mh_add(unsigned long long *t, uint32_t mask, int32_t y) {
+    const unsigned long long key = (unsigned long long)(uint32_t)y << 32;
+    uint32_t h = hash32((uint32_t)y) & mask;
+    for (uint32_t probe = 0; probe <= mask; probe++) {
+        unsigned long long w = __ldcg(t + h);
+        if (w == MH_EMPTY) {
+            w = atomicCAS(t + h, MH_EMPTY, key | 1ull);
+            if (w == MH_EMPTY) return 0;
+        }
+        if ((w & MH_KEY) == key) return (uint32_t)atomicAdd(t + h, 1ull);
+        h = (h + 1) & mask;
+    }
+    return 0xffffffffu;
+}
+
+__device__ __forceinline__ uint32_t mh_get(const unsigned long long *t, uint32_t mask, int32_t y) {
+    const unsigned long long key = (unsigned long long)(uint32_t)y << 32;
+    uint32_t h = hash32((uint32_t)y) & mask;
+    for (uint32_t probe = 0; probe <= mask; probe++) {
+        const unsigned long long w = __ldcg(t + h);
+        if ((w & MH_KEY) == key) return (uint32_t)w;
+        if (w == MH_EMPTY) return 0;
+        h = (h + 1) & mask;
+    }
+    return 0;
+}
+
+// Wedge prefix of the medium tier in shared memory: vertices of larger
+// degree walk their neighbours 32 at a time per warp instead.
+constexpr int MED_PCAP = 8192;
+
 template <int THREADS, bool CREDIT>
 __global__ void __launch_bounds__(THREADS)
 k_cycles_medium(CycleArgs a) {
     constexpr int NW = THREADS / 32;
-    __shared__ int32_t ntouched;
     __shared__ unsigned long long item[NW][WARP];
-    const int lane = lane_id(), warp = threadIdx.x >> 5;
+    __shared__ long long wsum[NW];
     __shared__ int32_t next;
+    extern __shared__ long long pre[];          // MED_PCAP + 1 entries
+    const int lane = lane_id(), warp = threadIdx.x >> 5;
     const int32_t nv = a.counters[C_MEDIUM];
-    uint32_t *tab = a.tables + (int64_t)blockIdx.x * a.n;
-    int32_t *tl = a.touched + (int64_t)blockIdx.x * a.n;
-    if (threadIdx.x == 0) { ntouched = 0; next = atomicAdd(a.counters + C_DYN, 1); }
+    unsigned long long *tab = a.mtab + (int64_t)blockIdx.x * a.mcap;
+    if (threadIdx.x == 0) next = atomicAdd(a.counters + C_DYN, 1);
     item[warp][lane] = 0;
     unsigned long long c4 = 0;
+    bool full = false;
     __syncthreads();
     while (true) {
         const int32_t idx = next;
         if (idx >= nv) break;
         const int32_t u = a.mlist[idx];
         const int32_t bu = a.rp[u], du = a.rp[u + 1] - bu;
-        warp_wedges(u, du, bu, warp * WARP, du, NW * WARP, a.rp, a.ci, a.nd,
-            [&](int k, int32_t q, int32_t y, bool ok, bool live) {
-                // the values returned by the increments of y sum to C(cnt[y], 2)
-                const uint32_t old = ok ? atomicAdd(tab + y, 1u) : 1u;
-                if (!CREDIT && ok) c4 += old;
-                const bool first = ok && old == 0;
-                const unsigned fm = __ballot_sync(FULL, first);
-                if (fm) {
-                    int32_t base = 0;
-                    if (lane == __ffs(fm) - 1) base = atomicAdd(&ntouched, __popc(fm));
-                    base = __shfl_sync(FULL, base, __ffs(fm) - 1);
-                    if (first) tl[base + __popc(fm & ((1u << lane) - 1))] = y;
+        uint32_t cap = 1024;
+        while ((int64_t)cap < 2 * a.west[u] && (int64_t)cap < a.mcap) cap <<= 1;
+        const uint32_t mask = cap - 1;
+        // count: cnt[y] += 1 (the values returned add up to C(cnt[y], 2));
+        // credit: cnt[y] - 1 to (v, y) and, summed per neighbour, to (u, v)
+        auto count = [&](int k, int32_t q, int32_t y, bool ok, bool live) {
+            if (!ok) return;
+            const uint32_t old = mh_add(tab, mask, y);
+            if (old == 0xffffffffu) full = true;
+            else if (!CREDIT) c4 += old;
+        };
+        auto credit = [&](int k, int32_t q, int32_t y, bool ok, bool live) {
+            const uint32_t c = ok ? mh_get(tab, mask, y) : 0;
+            if (c > 1) atomicAdd(a.yacc + q, (unsigned long long)(c - 1));
+            item_add(item[warp], k, c > 1 ? c - 1 : 0, live);
+        };
+        if (du <= MED_PCAP) {
+            // prefix of the wedge counts over N(u) (d_v for v below u)
+            long long carry = 0;
+            for (int32_t b0 = 0; b0 < du; b0 += THREADS) {
+                const int32_t i = b0 + threadIdx.x;
+                long long len = 0;
+                if (i < du) {
+                    const int32_t v = a.ci[bu + i], dv = a.nd[bu + i];
+                    if (precedes(dv, v, du, u)) len = dv;
                 }
-            },
-            [&](int32_t) {});
-        __syncthreads();
-        if (CREDIT) {
-            warp_wedges(u, du, bu, warp * WARP, du, NW * WARP, a.rp, a.ci, a.nd,
-                [&](int k, int32_t q, int32_t y, bool ok, bool live) {
-                    const uint32_t c = ok ? __ldcg(tab + y) : 0;
-                    if (c > 1) atomicAdd(a.yacc + q, (unsigned long long)(c - 1));
-                    item_add(item[warp], k, c > 1 ? c - 1 : 0, live);
-                },
-                [&](int32_t it) {
-                    __syncwarp();
-                    const unsigned long long s = item[warp][lane];
-                    if (s) { atomicAdd(a.yacc + bu + it + lane, s); item[warp][lane] = 0; }
-                    __syncwarp();
-                });
+                long long incl = len;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const long long y = __shfl_up_sync(FULL, incl, o);
+                    if (lane >= o) incl += y;
+                }
+                if (lane == 31) wsum[warp] = incl;
+                __syncthreads();
+                long long before = 0, all = 0;
+                for (int j = 0; j < NW; j++) { const long long t = wsum[j]; before += j < warp ? t : 0; all += t; }
+                if (i < du) pre[i] = carry + before + incl - len;
+                carry += all;
+                __syncthreads();
+            }
+            if (threadIdx.x == 0) pre[du] = carry;
             __syncthreads();
+            const long long W = carry;
+            // every warp takes an equal range of the wedges
+            for (int ph = 0; ph < (CREDIT ? 2 : 1); ph++) {
+                const long long w_lo = W * warp / NW, w_hi = W * (warp + 1) / NW;
+                if (w_lo < w_hi) {
+                    int32_t lo = 0, hi = du;
+                    while (lo < hi) {
+                        const int32_t mid = (lo + hi + 1) >> 1;
+                        if (pre[mid] <= w_lo) lo = mid; else hi = mid - 1;
+                    }
+                    for (int32_t j0 = lo; j0 < du && pre[j0] < w_hi; j0 += WARP) {
+                        // lane l: neighbour j0 + l, its wedges clipped to [w_lo, w_hi)
+                        const int32_t j = j0 + lane;
+                        int32_t len = 0, start = 0;
+                        if (j < du) {
+                            const long long p0 = pre[j], p1 = pre[j + 1];
+                            const long long s0 = max(p0, w_lo), e0 = min(p1, w_hi);
+                            if (e0 > s0) {
+                                len = (int32_t)(e0 - s0);
+                                start = a.rp[a.ci[bu + j]] + (int32_t)(s0 - p0);
+                            }
+                        }
+                        const int32_t incl = warp_incl_scan(len);
+                        const int32_t total = __shfl_sync(FULL, incl, 31);
+                        const int32_t excl = incl - len;
+                        for (int32_t w0 = 0; w0 < total; w0 += WARP) {
+                            const int32_t w = w0 + lane;
+                            int32_t k = 0;
+#pragma unroll
+                            for (int s = 16; s >= 1; s >>= 1) {
+                                const int32_t e = __shfl_sync(FULL, excl, k + s);
+                                if (e <= w) k += s;
+                            }
+                            const int32_t ks = __shfl_sync(FULL, start, k);
+                            const int32_t ke = __shfl_sync(FULL, excl, k);
+                            const bool live = w < total;
+                            bool ok = false;
+                            int32_t q = 0, y = 0;
+                            if (live) {
+                                q = ks + (w - ke);
+                                y = a.ci[q];
+                                ok = precedes(a.nd[q], y, du, u);
+                            }
+                            if (ph == 0) count(k, q, y, ok, live);
+                            else credit(k, q, y, ok, live);
+                        }
+                        if (ph == 1) {
+                            __syncwarp();
+                            const unsigned long long sv = item[warp][lane];
+                            if (sv) { atomicAdd(a.yacc + bu + j, sv); item[warp][lane] = 0; }
+                            __syncwarp();
+                        }
+                    }
+                }
+                __syncthreads();
+            }
+        } else {
+            warp_wedges(u, du, bu, warp * WARP, du, NW * WARP, a.rp, a.ci, a.nd, count, [&](int32_t) {});
+            __syncthreads();
+            if (CREDIT) {
+                warp_wedges(u, du, bu, warp * WARP, du, NW * WARP, a.rp, a.ci, a.nd, credit,
+                    [&](int32_t it) {
+                        __syncwarp();
+                        const unsigned long long sv = item[warp][lane];
+                        if (sv) { atomicAdd(a.yacc + bu + it + lane, sv); item[warp][lane] = 0; }
+                        __syncwarp();
+                    });
+                __syncthreads();
+            }
         }
-        const int32_t nt = ntouched;
-        for (int32_t i = threadIdx.x; i < nt; i += THREADS) tab[tl[i]] = 0;
+        ulonglong2 *t2 = reinterpret_cast<ulonglong2 *>(tab);
+        for (uint32_t i = threadIdx.x; i < cap / 2; i += THREADS) t2[i] = make_ulonglong2(MH_EMPTY, MH_EMPTY);
         __syncthreads();
-        if (threadIdx.x == 0) { ntouched = 0; next = atomicAdd(a.counters + C_DYN, 1); }
+        if (threadIdx.x == 0) next = atomicAdd(a.counters + C_DYN, 1);
         __syncthreads();
     }
+    if (full) atomicOr(a.status, ERR_CAPACITY);
     if (!CREDIT) {
         c4 = warp_sum(c4);
         if (lane == 0) add_u128(a.sums + 2 * (S_NUM + X_C4), 4 * c4);
@@ -937,14 +1062,12 @@ __global__ void k_hub_lengths(CycleArgs a) {
     }
 }
 
-constexpr int64_t HUB_CHUNK = 2048;   // wedges per work unit
-
 // Hub tier, phase PH (0 count, 1 credit): the batch's wedges form one flat
 // space (hub rows concatenated, each neighbour contributing its list); every
-// warp takes chunks of HUB_CHUNK consecutive wedges, finds the first
-// neighbour of its chunk by binary search in the prefix, and walks the
-// neighbours 32 at a time, clipping the lists that straddle the chunk ends.
-// Hub h counts into table h.
+// warp of the grid takes an equal range of it, finds the first neighbour of
+// its range by binary search in the prefix, and walks the neighbours 32 at a
+// time, clipping the lists that straddle the range ends.  Hub h counts into
+// table h.
 template <int PH>
 __global__ void __launch_bounds__(256)
 k_cycles_hub(CycleArgs a) {
@@ -954,10 +1077,12 @@ k_cycles_hub(CycleArgs a) {
     __syncwarp();
     const int64_t flat = a.hoff[a.nhub];
     const int64_t wtot = a.hpre[flat];
-    const int64_t units = (wtot + HUB_CHUNK - 1) / HUB_CHUNK;
-    for (int64_t unit = global_warp(); unit < units; unit += num_warps()) {
-        const int64_t w_lo = unit * HUB_CHUNK;
-        const int64_t w_hi = min(wtot, w_lo + HUB_CHUNK);
+    // every warp of the grid takes an equal share of the batch's wedges
+    const int64_t gw = global_warp(), gwn = num_warps();
+    {
+        const int64_t w_lo = wtot * gw / gwn;
+        const int64_t w_hi = wtot * (gw + 1) / gwn;
+        if (w_lo >= w_hi) return;
         // largest j with hpre[j] <= w_lo
         int64_t lo = 0, hi = flat;
         while (lo < hi) {
@@ -1092,6 +1217,8 @@ cudaError_t run_schedule(gd_graph *g, int32_t *counters_host) {
     const int32_t n = g->n;
     cudaError_t e = cudaMemsetAsync(w.counters, 0, C_NUM * sizeof(int32_t), g->stream);
     if (e) return e;
+    e = cudaMemsetAsync(w.west + n, 0, sizeof(int64_t), g->stream);   // largest medium W
+    if (e) return e;
     if (n > 0 && g->nnz > 0) {
         GD_LAUNCH(g, "k_neighbor_degree", k_neighbor_degree, grid_for(g->nnz, 256, sms * 16), 256, 0,
                   g->nnz, g->rp, g->ci, w.nd);
@@ -1112,6 +1239,8 @@ cudaError_t run_schedule(gd_graph *g, int32_t *counters_host) {
                   n, g->rp, g->ci, w.nd, w.dag_off, w.dag_col, w.dag_slot, w.dag_nd);
     }
     e = cudaMemcpyAsync(counters_host, w.counters, C_NUM * sizeof(int32_t), cudaMemcpyDeviceToHost, g->stream);
+    if (e) return e;
+    e = cudaMemcpyAsync(&w.medium_wmax, w.west + n, sizeof(int64_t), cudaMemcpyDeviceToHost, g->stream);
     if (e) return e;
     e = cudaStreamSynchronize(g->stream);
     if (e) return e;
@@ -1213,7 +1342,7 @@ cudaError_t run_tri_bound(gd_graph *g, int64_t *total) {
     Workspace &w = g->ws;
     const int32_t n = g->n;
     *total = 0;
-    if (n == 0) return cudaSuccess;
+    if (n == 0 || g->m == 0) return cudaSuccess;     // no out-lists were built
     GD_LAUNCH(g, "k_tri_bound", k_tri_bound, grid_for((int64_t)n * 32, 256, sms_of(g) * 16), 256, 0,
               n, w.dag_off, w.dag_col, w.scan_tmp);
     cudaError_t e = exclusive_scan_i64(g, w.scan_tmp, w.toff, n, w.scan_tmp + (n + 1));
@@ -1273,11 +1402,7 @@ int32_t hub_batch(gd_graph *g) {
     return (int32_t)b;
 }
 
-int32_t table_slots(gd_graph *g) {
-    const int32_t s = 2 * sms_of(g);
-    const int32_t b = hub_batch(g);
-    return s > b ? s : b;
-}
+int32_t table_slots(gd_graph *g) { return hub_batch(g); }
 
 // 4-cycles: credits (per_edge) or the 4-cycle total (global).
 cudaError_t run_cycles(gd_graph *g, bool per_edge, const int32_t *cnt) {
@@ -1293,7 +1418,7 @@ cudaError_t run_cycles(gd_graph *g, bool per_edge, const int32_t *cnt) {
     a.n = g->n; a.rp = g->rp; a.ci = g->ci; a.nd = w.nd;
     a.vlist = w.vlist; a.hubs = w.hubs; a.mlist = w.mlist; a.tlist = w.tlist; a.counters = w.counters;
     a.capmask = (uint32_t)(g->ctx->opt.smem_table_max - 1);
-    a.tables = w.wtab; a.touched = w.touched; a.tcount = w.tcount;
+    a.tables = w.wtab; a.mtab = w.mtab; a.mcap = w.mtab_cap; a.west = w.west; a.status = w.status;
     a.yacc = (unsigned long long *)w.yacc; a.sums = w.sums;
     a.hub0 = 0; a.nhub = 0;
     // hubs, in batches
@@ -1317,10 +1442,16 @@ cudaError_t run_cycles(gd_graph *g, bool per_edge, const int32_t *cnt) {
     }
     // medium tier
     if (cnt[C_MEDIUM] > 0) {
-        const int32_t slots = 2 * sms;    // two 1024-thread CTAs fit on an SM
+        const int32_t slots = w.mtab_ctas;    // two 1024-thread CTAs fit on an SM
         const unsigned grid = (unsigned)(cnt[C_MEDIUM] < slots ? cnt[C_MEDIUM] : slots);
-        if (per_edge) GD_LAUNCH(g, "k_cycles_medium", (k_cycles_medium<1024, true>), grid, 1024, 0, a);
-        else GD_LAUNCH(g, "k_cycles_medium", (k_cycles_medium<1024, false>), grid, 1024, 0, a);
+        const size_t smem = sizeof(long long) * (MED_PCAP + 1);
+        if (per_edge) {
+            if ((e = allow_smem(k_cycles_medium<1024, true>, smem))) return e;
+            GD_LAUNCH(g, "k_cycles_medium", (k_cycles_medium<1024, true>), grid, 1024, smem, a);
+        } else {
+            if ((e = allow_smem(k_cycles_medium<1024, false>, smem))) return e;
+            GD_LAUNCH(g, "k_cycles_medium", (k_cycles_medium<1024, false>), grid, 1024, smem, a);
+        }
     }
     // tiny tier
     if (cnt[C_TINY] > 0) {
