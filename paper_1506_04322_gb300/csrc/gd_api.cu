@@ -242,6 +242,14 @@ size_t estimate_footprint(gd_ctx *ctx, int64_t n, int64_t nnz, bool per_edge, bo
     for (const AllocSpec &a : sp) b += round_block(a.bytes);
     if (per_edge && host_out) b += round_block(sizeof(uint64_t) * 15 * (size_t)(nnz / 2));
     if (n > 0) b += round_block(clique_pairs_bound(ctx ? ctx->num_sms : 152, n));
+    if (n > 0) {
+        // medium-tier tables: W(u) <= min(2^hub, nnz) entries, two per SM
+        const int64_t hub = int64_t(1) << (ctx ? ctx->opt.hub_wedges_log2 : 18);
+        int64_t cap = 1024;
+        while (cap < 2 * std::min<int64_t>(hub, nnz)) cap <<= 1;
+        const int64_t ctas = std::min<int64_t>(2 * (ctx ? ctx->num_sms : 152), n);
+        b += round_block(sizeof(unsigned long long) * (size_t)(cap * ctas));
+    }
     if (per_edge) b += round_block(sizeof(unsigned long long) * 2 * (size_t)nnz);   // triangle records (typical)
     g.ws = Workspace();
     return b;
