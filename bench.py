@@ -208,13 +208,14 @@ def algorithmic_bytes(g, triangles: int, per_edge: bool) -> dict:
 
 
 def source_digest() -> str:
+    """Digest of the sources of the bitmap and 4-cycle kernels (the families
+    whose DRAM traffic is taken from a committed ncu summary)."""
     import hashlib
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1506_04322_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh", ".h")):
-            with open(os.path.join(csrc, f), "rb") as fh:
-                h.update(fh.read())
+    for f in ("gd_step2.cu", "gd_device.cuh"):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(fh.read())
     return h.hexdigest()[:16]
 
 
@@ -577,6 +578,7 @@ def run_gd(args):
         "batch": batch,
         "serving": serving,
         "kernels": {k: round(v["ms_total"] / args.steps, 3) for k, v in sorted(kern.items(), key=lambda kv: -kv[1]["ms_total"])},
+        "kernel_launches_per_step": {k: v["launches"] // args.steps for k, v in kern.items()},
         "source_digest": source_digest(),
         "global_counts": [str(x) for x in glob],
     }
