@@ -299,6 +299,55 @@ int gd_serve_stop(gd_ctx *ctx);
 int gd_footprint_estimate(gd_ctx *ctx, int32_t n, int64_t nnz, int per_edge, size_t *bytes);
 
 /* ------------------------------------------------------------------------
+ * Ranking by graphlet counts (Sec. 6 and Fig. 6: the edges and nodes with
+ * the most triangles, 4-cliques, stars, ... surfaced for analysis).
+ * ------------------------------------------------------------------------ */
+
+/* The k largest of values[i * stride], 0 <= i < count (uint64): indices to
+ * idx_out (int64) and values to val_out (nullable), both host arrays of k
+ * entries, ordered by value descending and, among equal values, by index
+ * ascending, so the answer is unique.  values is device memory when flags
+ * has GD_DEVICE_PTRS, else host memory (copied in).  Work runs on
+ * cuda_stream (NULL: legacy default stream); scratch comes from the
+ * context's cache and budget.  0 <= k <= count, stride >= 1.
+ * For the edges with the most 4-cliques: values = per-edge matrix + 4,
+ * stride 15, count = m (row i is the i-th edge of gd_count_per_edge). */
+int gd_topk(gd_ctx *ctx, const uint64_t *values, int64_t count, int64_t stride, int flags, int64_t k,
+            int64_t *idx_out, uint64_t *val_out, void *cuda_stream);
+
+/* For every node v, the sum over the edges e incident to v of
+ * per_edge[e * 15 + column] (per_edge: the m x 15 matrix gd_count_per_edge
+ * wrote for this graph; device memory with GD_DEVICE_PTRS in flags, else
+ * host).  Column 0 gives twice the number of triangles at v; column 4 three
+ * times the 4-cliques at v.  node_out: n uint64, device memory with
+ * GD_OUT_DEVICE in out_flags, else host.  The graph must have been counted
+ * per edge (GD_EINVAL otherwise). */
+int gd_node_sums(gd_graph *g, const uint64_t *per_edge, int flags, int column, uint64_t *node_out,
+                 int out_flags);
+
+/* ------------------------------------------------------------------------
+ * Graphlet frequency features (Sec. 6: graph classification with graphlet
+ * features; Table 1 sizes k = 2, 3, 4).
+ * ------------------------------------------------------------------------ */
+
+/* The 17 normalised frequencies of a graph with n nodes, m edges and the
+ * 15 exact counts of gd_count_global:
+ *   out[0] = m / C(n,2), out[1] = (C(n,2) - m) / C(n,2)      (k = 2)
+ *   out[2..5]  = g31..g34 / C(n,3)
+ *   out[6..16] = g41..g4_11 / C(n,4)
+ * Each value is the exact rational rounded once to the nearest double, ties
+ * to even; a size with no subsets (C(n,k) = 0) gives 0.  Host only.
+ * GD_EINVAL for n < 0, m < 0 or m > C(n,2). */
+int gd_gfd(int64_t n, int64_t m, const gd_u128 counts[15], double out[17]);
+
+/* The same for the num_graphs graphs of a batch on the GPU: graph_node_ptr
+ * and row_ptr as given to gd_count_batch, counts the num_graphs x 15 uint64
+ * it wrote, out num_graphs x 17 doubles.  All DEVICE pointers (flags must
+ * have GD_DEVICE_PTRS); runs on cuda_stream and waits for it. */
+int gd_gfd_batch(gd_ctx *ctx, int32_t num_graphs, const int32_t *graph_node_ptr, const int32_t *row_ptr,
+                 const uint64_t *counts, int flags, double *out, void *cuda_stream);
+
+/* ------------------------------------------------------------------------
  * Counting without allocating (no counterpart in the paper).
  *
  * For callers that must not allocate device memory: code running next to a

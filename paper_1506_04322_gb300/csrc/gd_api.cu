@@ -227,6 +227,10 @@ int ensure_workspace(gd_graph *g, bool per_edge) {
 
 namespace gdi {
 
+// Device bytes the medium tier's tables may take for a graph of nnz slots
+// (64 per slot, at least 64 MB): fewer CTAs share the tier beyond that.
+int64_t medium_table_limit(int64_t nnz) { return std::max<int64_t>(int64_t(64) << 20, 64 * nnz); }
+
 // Device bytes a graph of n rows and nnz slots holds after one count call
 // (CSR copy included); per_edge adds the per-edge arrays and the staging of
 // a host-side output matrix.
@@ -243,17 +247,23 @@ size_t estimate_footprint(gd_ctx *ctx, int64_t n, int64_t nnz, bool per_edge, bo
     if (per_edge && host_out) b += round_block(sizeof(uint64_t) * 15 * (size_t)(nnz / 2));
     if (n > 0) b += round_block(clique_pairs_bound(ctx ? ctx->num_sms : 152, n));
     if (n > 0) {
-        // medium-tier tables: W(u) <= min(2^hub, nnz) entries, two per SM
+        // medium-tier tables: W(u) <= min(2^hub, nnz) entries, two per SM,
+        // within the per-graph limit
         const int64_t hub = int64_t(1) << (ctx ? ctx->opt.hub_wedges_log2 : 18);
         int64_t cap = 1024;
         while (cap < 2 * std::min<int64_t>(hub, nnz)) cap <<= 1;
         const int64_t ctas = std::min<int64_t>(2 * (ctx ? ctx->num_sms : 152), n);
-        b += round_block(sizeof(unsigned long long) * (size_t)(cap * ctas));
+        b += round_block((size_t)std::min<int64_t>(8 * cap * ctas, std::max<int64_t>(8 * cap, medium_table_limit(nnz))));
     }
     if (per_edge) b += round_block(sizeof(unsigned long long) * 2 * (size_t)nnz);   // triangle records (typical)
     g.ws = Workspace();
     return b;
 }
+
+// Scratch through the context's cache and budget (for calls outside a
+// graph's workspace).
+int scratch_alloc(gd_ctx *ctx, void **p, size_t bytes) { return ctx_alloc(ctx, p, bytes); }
+void scratch_release(gd_ctx *ctx, void *p, size_t bytes) { ctx_release(ctx, p, bytes); }
 
 }  // namespace gdi
 
@@ -314,13 +324,15 @@ int ensure_records(gd_graph *g, int64_t total) {
 
 // Per-CTA tables of the medium tier: a power of two >= 2 W entries for the
 // largest medium vertex, one per CTA (two per SM, fewer when there are fewer
-// vertices or the tables would pass 8 GB), all entries empty (all ones).
+// vertices or the tables would pass medium_table_limit), all entries empty
+// (all ones).
 int ensure_medium_scratch(gd_graph *g, const int32_t *cnt) {
     Workspace &w = g->ws;
     int64_t cap = 1024;
     while (cap < 2 * w.medium_wmax) cap <<= 1;
     int64_t ctas = std::min<int64_t>(2 * g->ctx->num_sms, cnt[C_MEDIUM]);
-    while (ctas > 1 && ctas * cap * 8 > (int64_t(8) << 30)) ctas /= 2;
+    const int64_t limit = medium_table_limit(g->nnz);
+    while (ctas > 1 && ctas * cap * 8 > limit) ctas--;
     if (w.mtab && w.mtab_cap >= cap && w.mtab_ctas >= ctas) return GD_OK;
     if (w.mtab) { release_block(g, w.mtab); w.mtab = nullptr; w.mtab_cap = 0; w.mtab_ctas = 0; }
     int rc = dalloc(g, (void **)&w.mtab, sizeof(unsigned long long) * (size_t)(ctas * cap));
@@ -650,6 +662,7 @@ static int count_path(gd_graph *g, bool per_edge, uint64_t *out_dev) {
     int rc = ensure_workspace(g, per_edge);
     if (rc) return rc;
     GD_CK(ctx, prepare_edges(g));
+    g->prepared = true;                  // edge list (row order of the per-edge output) in place
     if (variant == GD_VARIANT_LITERAL) {
         if ((rc = ensure_tribuf(g, variant))) return rc;
         GD_CK(ctx, run_triangles_intersect(g));

@@ -174,12 +174,19 @@ struct gd_graph {
     bool borrowed = false;
     size_t csr_bytes = 0;
     int32_t max_deg = 0;
-    bool prepared = false;       // edge list / mate / T computed
-    bool per_edge_ready = false; // per-edge arrays allocated
+    bool prepared = false;       // edge list (eu, ev: rows of the per-edge output) built
     gdi::Workspace ws;
 };
 
 namespace gdi {
+
+// exclusive scan of len int64 values, out[len] = total (gd_count.cu); tmp
+// needs 2 * ceil(len / 1024) + 64 entries per level
+cudaError_t exclusive_scan_i64(gd_graph *g, const int64_t *in, int64_t *out, int64_t len, int64_t *tmp);
+
+// device scratch through the context's cache and budget (gd_api.cu)
+int scratch_alloc(gd_ctx *ctx, void **p, size_t bytes);
+void scratch_release(gd_ctx *ctx, void *p, size_t bytes);
 
 // launch bookkeeping (gd_api.cu): launch counter and, while profiling, an
 // event pair around the launch on the graph's stream
@@ -203,6 +210,7 @@ cudaError_t run_node_sums(gd_graph *g);                                      // 
 size_t clique_big_bytes(int32_t dm);
 cudaError_t clique_pairs_bytes(gd_graph *g, const int32_t *counters_host, size_t *need);
 cudaError_t run_tri_bound(gd_graph *g, int64_t *total);
+int64_t medium_table_limit(int64_t nnz);
 size_t clique_pairs_bound(int sms, int64_t n);                                         // per CTA
 cudaError_t run_cycles(gd_graph *g, bool per_edge, const int32_t *counters_host);
 int32_t table_slots(gd_graph *g);

@@ -146,8 +146,11 @@ void worker_main(Service *s, int32_t k) {
     while (true) {
         {
             std::unique_lock<std::mutex> lk(s->mu);
+            // the requests of the previous round may be gone (polled and freed):
+            // only what pick() hands out in this round is run
+            work.clear();
             s->cv_work.wait(lk, [&] { return s->stop || pick(s, work); });
-            if (work.empty()) break;      // stop requested and nothing picked
+            if (s->stop && work.empty()) break;      // stop requested and nothing picked
             const double t = s->now_ms();
             for (Request *r : work) { r->state = 1; r->t_start = t; r->slot = k; r->batched = work.size() > 1 || r->n <= SMALL_N; }
         }

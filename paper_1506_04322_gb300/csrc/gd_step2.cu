@@ -470,8 +470,8 @@ k_clique_bitmap(CliqueArgs a) {
 
         if (MODE == MODE_TRISUM) {
             const unsigned long long da = (unsigned long long)(a.rp[va + 1] - a.rp[va]);
-            auto tri = [&](int32_t kc, int32_t kx, int32_t s) {
-                const unsigned long long P = (unsigned long long)S.acc[kc] + S.acc[kx] + __ldg(a.tslot + s);
+            auto tri_t = [&](int32_t kc, int32_t kx, int32_t s, uint32_t tcx) {
+                const unsigned long long P = (unsigned long long)S.acc[kc] + S.acc[kx] + tcx;
                 const unsigned long long R = da + (unsigned long long)S.adeg[kc] + (unsigned long long)S.adeg[kx];
                 atomicAdd(a.qcred + 2 * (int64_t)s, P);
                 atomicAdd(a.qcred + 2 * (int64_t)s + 1, R);
@@ -482,13 +482,29 @@ k_clique_bitmap(CliqueArgs a) {
             };
             if (scan) {
                 scan_pairs<TW>(a, S, D, bits, fbits, tw, [&](int32_t kc, int32_t kx, int32_t q) {
-                    tri(kc, kx, ldg(a.dag_slot + q));
+                    const int32_t s = ldg(a.dag_slot + q);
+                    tri_t(kc, kx, s, __ldg(a.tslot + s));
                 });
             } else {
+                // four records per lane at a time: their |Tri| gathers in flight together
                 const unsigned long long *rec = a.recs + a.toff[va];
-                for (int32_t i = tt; i < ne; i += TW * 32) {
+                constexpr int32_t ST = TW * 32;
+                int32_t i = tt;
+                for (; i + 3 * ST < ne; i += 4 * ST) {
+                    unsigned long long v[4];
+                    uint32_t t[4];
+#pragma unroll
+                    for (int j = 0; j < 4; j++) v[j] = rec[i + j * ST];
+#pragma unroll
+                    for (int j = 0; j < 4; j++) t[j] = __ldg(a.tslot + (int32_t)(v[j] >> 32));
+#pragma unroll
+                    for (int j = 0; j < 4; j++)
+                        tri_t((int32_t)(v[j] & 0xffffu), (int32_t)((v[j] >> 16) & 0xffffu), (int32_t)(v[j] >> 32), t[j]);
+                }
+                for (; i < ne; i += ST) {
                     const unsigned long long v = rec[i];
-                    tri((int32_t)(v & 0xffffu), (int32_t)((v >> 16) & 0xffffu), (int32_t)(v >> 32));
+                    const int32_t s = (int32_t)(v >> 32);
+                    tri_t((int32_t)(v & 0xffffu), (int32_t)((v >> 16) & 0xffffu), s, __ldg(a.tslot + s));
                 }
             }
             team_sync();
@@ -1203,7 +1219,6 @@ cudaError_t allow_smem(K kernel, size_t bytes) {
 
 static int sms_of(gd_graph *g) { return g->ctx->num_sms > 0 ? g->ctx->num_sms : 152; }
 
-cudaError_t exclusive_scan_i64(gd_graph *g, const int64_t *in, int64_t *out, int64_t len, int64_t *tmp);
 
 __global__ void k_narrow_i32(const int64_t *in, int32_t *out, int64_t len) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < len; i += (int64_t)gridDim.x * blockDim.x)

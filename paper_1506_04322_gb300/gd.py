@@ -116,6 +116,10 @@ def load():
             "gd_autotune": (ctypes.c_int, [vp, ctypes.c_int, i32, vp]),
             "gd_set_options": (ctypes.c_int, [vp, vp]),
             "gd_get_options": (ctypes.c_int, [vp, vp]),
+            "gd_topk": (ctypes.c_int, [vp, vp, i64, i64, ctypes.c_int, i64, vp, vp, vp]),
+            "gd_node_sums": (ctypes.c_int, [vp, vp, ctypes.c_int, ctypes.c_int, vp, ctypes.c_int]),
+            "gd_gfd": (ctypes.c_int, [i64, i64, vp, vp]),
+            "gd_gfd_batch": (ctypes.c_int, [vp, i32, vp, vp, vp, ctypes.c_int, vp, vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -239,6 +243,40 @@ def gd_count_global_static(n: int, nnz: int, row_ptr: int, col_idx: int, out: in
     """Global counts without allocating (device pointers in and out; see
     include/gd.h).  Returns the gd_status code."""
     return int(load().gd_count_global_static(n, nnz, row_ptr, col_idx, out, stream or None))
+
+
+def gd_topk(ctx, values_ptr: int, count: int, stride: int, k: int, device: bool, stream: int = 0):
+    """(indices int64[k], values uint64[k]) of the k largest values[i * stride],
+    value descending, ties by ascending index."""
+    idx = np.zeros(max(k, 1), dtype=np.int64)
+    val = np.zeros(max(k, 1), dtype=np.uint64)
+    _check(ctx, load().gd_topk(ctx, values_ptr, count, stride, GD_DEVICE_PTRS if device else 0, k,
+                               idx.ctypes.data, val.ctypes.data, stream or None), "gd_topk")
+    return idx[:k], val[:k]
+
+
+def gd_node_sums(ctx, graph, per_edge_ptr: int, device: bool, column: int, out_ptr: int, out_device: bool) -> None:
+    _check(ctx, load().gd_node_sums(graph, per_edge_ptr, GD_DEVICE_PTRS if device else 0, column, out_ptr,
+                                    GD_OUT_DEVICE if out_device else 0), "gd_node_sums")
+
+
+def gd_gfd(n: int, m: int, counts) -> np.ndarray:
+    """17 normalised frequencies (k = 2, 3, 4) from the 15 exact counts."""
+    c = (gd_u128 * 15)()
+    for i, x in enumerate(counts):
+        c[i].lo = int(x) & (2**64 - 1)
+        c[i].hi = int(x) >> 64
+    out = np.zeros(17, dtype=np.float64)
+    rc = load().gd_gfd(n, m, c, out.ctypes.data)
+    if rc != GD_OK:
+        raise GDError(rc, "gd_gfd: invalid arguments")
+    return out
+
+
+def gd_gfd_batch(ctx, num_graphs: int, graph_node_ptr: int, row_ptr: int, counts: int, out: int,
+                 stream: int = 0) -> None:
+    _check(ctx, load().gd_gfd_batch(ctx, num_graphs, graph_node_ptr, row_ptr, counts, GD_DEVICE_PTRS, out,
+                                    stream or None), "gd_gfd_batch")
 
 
 def gd_autotune(ctx, graph, per_edge: bool = False, max_trials: int = 24) -> dict:
@@ -404,6 +442,16 @@ class Context:
     def footprint_estimate(self, n: int, nnz: int, per_edge: bool = False) -> int:
         return gd_footprint_estimate(self.handle, n, nnz, per_edge)
 
+    def topk(self, values, k: int, column: int | None = None):
+        """The k largest entries (indices, values), value descending and ties
+        by ascending index.  values: uint64 vector, or an [rows, 15] per-edge
+        matrix with `column` chosen (numpy on the host or torch on the GPU)."""
+        ptr, dev = _ptr(values)
+        if column is not None:
+            rows, cols = values.shape
+            return gd_topk(self.handle, ptr + 8 * column, rows, cols, k, dev)
+        return gd_topk(self.handle, ptr, int(values.shape[0]), 1, k, dev)
+
     def graph(self, row_ptr, col_idx=None, n: int | None = None, validate: bool = False,
               borrow: bool = False, stream: int | None = None) -> "Graph":
         """Upload a CSR graph: numpy arrays, torch tensors, or an object with
@@ -483,6 +531,16 @@ class Graph:
 
     def count_global(self) -> list[int]:
         return gd_count_global(self.ctx.handle, self.handle)
+
+    def node_sums(self, per_edge, column: int, out=None):
+        """Per node v, the sum of column `column` of the per-edge matrix over
+        the edges at v (numpy or torch CUDA in and out)."""
+        pp, pdev = _ptr(per_edge)
+        if out is None:
+            out = np.zeros(max(self.n, 1), dtype=np.uint64)
+        po, odev = _ptr(out)
+        gd_node_sums(self.ctx.handle, self.handle, pp, pdev, column, po, odev)
+        return out[:self.n]
 
     def count_per_edge(self, out=None, want_global: bool = True):
         """uint64 [m, 15] per-edge counts (numpy on the host, or into the given
