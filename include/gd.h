@@ -299,6 +299,21 @@ int gd_serve_stop(gd_ctx *ctx);
 int gd_footprint_estimate(gd_ctx *ctx, int32_t n, int64_t nnz, int per_edge, size_t *bytes);
 
 /* ------------------------------------------------------------------------
+ * Local update of the counts when one edge is inserted or deleted (the
+ * paper's closing remarks on dynamic graphs; only the subsets that contain
+ * both end nodes change).
+ * ------------------------------------------------------------------------ */
+
+/* Toggle the pair {u, v} of g (delete it if it is an edge, insert it if not)
+ * and report, per graphlet (Table 1 order), how many 3-/4-node subsets enter
+ * it (gain) and leave it (loss): the counts of the toggled graph are
+ * count + gain - loss, exactly.  Work is proportional to the neighbourhoods
+ * of u and v and their neighbours' lists (no full recount).  The graph
+ * itself is not modified; *was_edge (nullable) says which way the toggle
+ * went.  GD_EINVAL if u == v or either is out of range. */
+int gd_toggle_delta(gd_graph *g, int32_t u, int32_t v, gd_u128 gain[15], gd_u128 loss[15], int *was_edge);
+
+/* ------------------------------------------------------------------------
  * Ranking by graphlet counts (Sec. 6 and Fig. 6: the edges and nodes with
  * the most triangles, 4-cliques, stars, ... surfaced for analysis).
  * ------------------------------------------------------------------------ */

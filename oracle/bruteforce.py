@@ -100,3 +100,27 @@ def per_edge_counts(g) -> list[list[int]]:
             if v > u:
                 rows.append(edge_counts(adj, u, v))
     return rows
+
+
+def toggle_gain_loss(g, u: int, v: int) -> tuple[list[int], list[int]]:
+    """For the pair {u, v} toggled (deleted if an edge, inserted if not): per
+    graphlet, the number of 3- and 4-node subsets that enter it (gain) and
+    leave it (loss).  Only subsets holding both u and v change; each is
+    classified before and after from the definitions.  O(n^2) subsets."""
+    adj = adjacency_sets(g)
+    after = [set(s) for s in adj]
+    if v in after[u]:
+        after[u].discard(v); after[v].discard(u)
+    else:
+        after[u].add(v); after[v].add(u)
+    gain = {name: 0 for name in ORDER}
+    loss = {name: 0 for name in ORDER}
+    others = [w for w in range(g.n) if w != u and w != v]
+    subsets = [(u, v, w) for w in others]
+    subsets += [(u, v, w, r) for w, r in itertools.combinations(others, 2)]
+    for s in subsets:
+        a, b = classify(s, adj), classify(s, after)
+        if a != b:
+            loss[a] += 1
+            gain[b] += 1
+    return [gain[x] for x in ORDER], [loss[x] for x in ORDER]

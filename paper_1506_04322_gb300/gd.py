@@ -117,6 +117,7 @@ def load():
             "gd_set_options": (ctypes.c_int, [vp, vp]),
             "gd_get_options": (ctypes.c_int, [vp, vp]),
             "gd_topk": (ctypes.c_int, [vp, vp, i64, i64, ctypes.c_int, i64, vp, vp, vp]),
+            "gd_toggle_delta": (ctypes.c_int, [vp, i32, i32, vp, vp, ctypes.POINTER(ctypes.c_int)]),
             "gd_node_sums": (ctypes.c_int, [vp, vp, ctypes.c_int, ctypes.c_int, vp, ctypes.c_int]),
             "gd_gfd": (ctypes.c_int, [i64, i64, vp, vp]),
             "gd_gfd_batch": (ctypes.c_int, [vp, i32, vp, vp, vp, ctypes.c_int, vp, vp]),
@@ -243,6 +244,15 @@ def gd_count_global_static(n: int, nnz: int, row_ptr: int, col_idx: int, out: in
     """Global counts without allocating (device pointers in and out; see
     include/gd.h).  Returns the gd_status code."""
     return int(load().gd_count_global_static(n, nnz, row_ptr, col_idx, out, stream or None))
+
+
+def gd_toggle_delta(ctx, graph, u: int, v: int):
+    """(gain, loss, was_edge) of toggling the pair {u, v}: counts after the
+    toggle = counts + gain - loss."""
+    gain, loss = (gd_u128 * 15)(), (gd_u128 * 15)()
+    was = ctypes.c_int()
+    _check(ctx, load().gd_toggle_delta(graph, u, v, gain, loss, ctypes.byref(was)), "gd_toggle_delta")
+    return _u128_list(gain), _u128_list(loss), bool(was.value)
 
 
 def gd_topk(ctx, values_ptr: int, count: int, stride: int, k: int, device: bool, stream: int = 0):
@@ -531,6 +541,10 @@ class Graph:
 
     def count_global(self) -> list[int]:
         return gd_count_global(self.ctx.handle, self.handle)
+
+    def toggle_delta(self, u: int, v: int):
+        """(gain, loss, was_edge) of inserting or deleting the pair {u, v}."""
+        return gd_toggle_delta(self.ctx.handle, self.handle, u, v)
 
     def node_sums(self, per_edge, column: int, out=None):
         """Per node v, the sum of column `column` of the per-edge matrix over
