@@ -278,11 +278,66 @@ def run_batch_measure(gd, torch, ctx, device, steps: int, loop_graphs: int = 600
     for i, r in enumerate(loop_res):
         if [int(x) for x in res[i]] != r:
             raise RuntimeError(f"batched and per-graph counts differ on graph {i}")
+    # graphlet frequency features of every graph of the batch (17 doubles each)
+    feats = torch.empty((G, 17), dtype=torch.float64, device=device)
+    gd.gd_gfd_batch(ctx.handle, G, db.graph_node_ptr.data_ptr(), db.row_ptr.data_ptr(), out.data_ptr(), feats.data_ptr())
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        gd.gd_gfd_batch(ctx.handle, G, db.graph_node_ptr.data_ptr(), db.row_ptr.data_ptr(), out.data_ptr(),
+                        feats.data_ptr())
+    torch.cuda.synchronize()
+    dt_gfd = (time.perf_counter() - t0) / steps
     return {"workload": "graph_batch_20000 (n~U[20,500], half ER mean degree U[2,12], half BA m in {1,2,3})",
             "graphs": G, "nodes": int(b.graph_node_ptr[-1]), "edges": int(b.row_ptr[-1]) // 2,
             "graphs_per_s": G / dt, "ms_per_batch": 1000 * dt, "e2e_graphs_per_s": G / dt_e2e,
             "per_graph_loop_graphs_per_s": 1.0 / dt_loop, "per_graph_loop_sample": len(sub),
-            "speedup_vs_loop": (G / dt) * dt_loop}
+            "speedup_vs_loop": (G / dt) * dt_loop,
+            "features_ms_per_batch": 1000 * dt_gfd, "features_graphs_per_s": G / dt_gfd}
+
+
+def run_next_measure(gd, torch, ctx, h, g, out) -> dict:
+    """Edge insert/delete updates and ranking on the single-graph workload:
+    toggles per second (random edges, random non-edges, pairs of hubs)
+    against one full global recount, and top-k / node-sum times over the
+    per-edge matrix already in HBM."""
+    rng = np.random.default_rng(8)
+    e = g.edges()
+    deg = g.degrees()
+    hubs = np.argsort(-deg)[:8]
+    pairs = [tuple(int(x) for x in e[i]) for i in rng.choice(len(e), 100, replace=False)]
+    pairs += [(int(a), int(b)) for a, b in rng.integers(0, g.n, size=(100, 2)) if a != b]
+    hub_pairs = [(int(hubs[i]), int(hubs[j])) for i in range(8) for j in range(i + 1, 8)]
+    h.toggle_delta(*pairs[0])
+    t0 = time.perf_counter()
+    for u, v in pairs:
+        h.toggle_delta(u, v)
+    dt_pair = (time.perf_counter() - t0) / len(pairs)
+    t0 = time.perf_counter()
+    for u, v in hub_pairs:
+        h.toggle_delta(u, v)
+    dt_hub = (time.perf_counter() - t0) / len(hub_pairs)
+    h.count_global()
+    t0 = time.perf_counter()
+    h.count_global()
+    dt_full = time.perf_counter() - t0
+    ctx.topk(out, 1000, column=4)
+    t0 = time.perf_counter()
+    for _ in range(5):
+        ctx.topk(out, 1000, column=4)
+    dt_topk = (time.perf_counter() - t0) / 5
+    node = torch.empty(g.n, dtype=torch.int64, device=out.device)
+    h.node_sums(out, 0, out=node)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(5):
+        h.node_sums(out, 0, out=node)
+    torch.cuda.synchronize()
+    dt_node = (time.perf_counter() - t0) / 5
+    return {"toggle_ms_random_pair": 1000 * dt_pair, "toggle_ms_hub_pair": 1000 * dt_hub,
+            "full_global_recount_ms": 1000 * dt_full, "toggles_per_s": 1.0 / dt_pair,
+            "topk1000_ms_4clique_column": 1000 * dt_topk, "node_sums_ms": 1000 * dt_node,
+            "pairs": f"{len(pairs)} random (100 edges, the rest non-edges), {len(hub_pairs)} pairs of the 8 largest hubs"}
 
 
 def run_serving_measure(gd, count: int = 200, load: float = 0.7, slots: int = 4, seed: int = 5) -> dict:
@@ -547,6 +602,9 @@ def run_gd(args):
                                    "achieved_gbs": ab[f] / (fam_ms[f] / 1000.0) / 1e9 if fam_ms[f] else None}
                                for f in fam_ms if f != dom}}
 
+    nxt = None
+    if not args.global_only and not args.no_batch:
+        nxt = run_next_measure(gd, torch, ctx, h, g, out)
     batch = None
     if not args.no_batch:
         batch = run_batch_measure(gd, torch, ctx, device, max(2, min(args.steps, 5)))
@@ -577,6 +635,7 @@ def run_gd(args):
         "clocks": clk,
         "batch": batch,
         "serving": serving,
+        "updates_and_ranking": nxt,
         "kernels": {k: round(v["ms_total"] / args.steps, 3) for k, v in sorted(kern.items(), key=lambda kv: -kv[1]["ms_total"])},
         "kernel_launches_per_step": {k: v["launches"] // args.steps for k, v in kern.items()},
         "source_digest": source_digest(),
