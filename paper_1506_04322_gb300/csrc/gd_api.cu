@@ -343,21 +343,29 @@ int ensure_medium_scratch(gd_graph *g, const int32_t *cnt) {
     return GD_OK;
 }
 
-// Flat neighbour lists of a hub batch: lengths, prefix, scan scratch.
-int ensure_hub_scratch(gd_graph *g) {
+// Flat neighbour lists of the hubs: row offsets (from the hub list), then
+// lengths, prefix and scan scratch sized to the hubs' concatenated rows.
+int ensure_hub_scratch(gd_graph *g, const int32_t *cnt) {
     Workspace &w = g->ws;
-    const int64_t cap = (int64_t)hub_batch(g) * std::max<int32_t>(g->max_deg, 1);
-    if (w.hub_off && w.hub_flat_cap >= cap) return GD_OK;
+    const int32_t nh = cnt[C_HUB];
     int rc;
-    if (w.hub_off) {
-        release_block(g, w.hub_off); release_block(g, w.hub_len); release_block(g, w.hub_pre);
-        release_block(g, w.hub_scan_tmp);
+    if (!w.hub_off || w.hub_off_cap < nh + 1) {
+        if (w.hub_off) { release_block(g, w.hub_off); w.hub_off = nullptr; }
+        if ((rc = dalloc_n(g, &w.hub_off, (int64_t)nh + 1))) return rc;
+        w.hub_off_cap = nh + 1;
     }
-    if ((rc = dalloc_n(g, &w.hub_off, 64))) return rc;
-    if ((rc = dalloc_n(g, &w.hub_len, cap))) return rc;
-    if ((rc = dalloc_n(g, &w.hub_pre, cap + 1))) return rc;
-    if ((rc = dalloc_n(g, &w.hub_scan_tmp, 2 * (cap / 2048 + 1) + 4096))) return rc;
-    w.hub_flat_cap = cap;
+    int64_t flat = 0;
+    GD_CK(g->ctx, run_hub_offsets(g, nh, &flat));
+    w.hub_flat = flat;
+    if (w.hub_len && w.hub_flat_cap >= flat) return GD_OK;
+    if (w.hub_len) {
+        release_block(g, w.hub_len); release_block(g, w.hub_pre); release_block(g, w.hub_scan_tmp);
+        w.hub_len = w.hub_pre = w.hub_scan_tmp = nullptr;
+    }
+    if ((rc = dalloc_n(g, &w.hub_len, flat))) return rc;
+    if ((rc = dalloc_n(g, &w.hub_pre, flat + 1))) return rc;
+    if ((rc = dalloc_n(g, &w.hub_scan_tmp, 2 * (flat / 2048 + 1) + 4096))) return rc;
+    w.hub_flat_cap = flat;
     return GD_OK;
 }
 
@@ -675,7 +683,7 @@ static int count_path(gd_graph *g, bool per_edge, uint64_t *out_dev) {
     int32_t cnt[C_NUM];
     GD_CK(ctx, run_schedule(g, cnt));
     if (cnt[C_CL0 + 3] > 0 && (rc = ensure_clique_scratch(g, cnt))) return rc;
-    if (cnt[C_HUB] > 0 && (rc = ensure_hub_scratch(g))) return rc;
+    if (cnt[C_HUB] > 0 && (rc = ensure_hub_scratch(g, cnt))) return rc;
     if (cnt[C_MEDIUM] > 0 && (rc = ensure_medium_scratch(g, cnt))) return rc;
     if ((rc = ensure_pairs(g, cnt))) return rc;
     if (per_edge) {

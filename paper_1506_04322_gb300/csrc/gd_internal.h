@@ -99,7 +99,9 @@ struct Workspace {
     int32_t cbig_dm = 0, cbig_ctas = 0;
     int32_t *mlist = nullptr;      // [n] medium tier sorted by decreasing wedge work
     int64_t *hub_off = nullptr, *hub_len = nullptr, *hub_pre = nullptr, *hub_scan_tmp = nullptr;
-    int64_t hub_flat_cap = 0;      // hub batch size x largest degree
+    int64_t hub_flat_cap = 0;      // capacity of hub_len / hub_pre
+    int64_t hub_flat = 0;          // the hubs' concatenated rows (this count call)
+    int32_t hub_off_cap = 0;       // capacity of hub_off
     int32_t *tlist = nullptr;      // [n] tiny tier (warp per vertex)
     int64_t *west = nullptr;       // [n] wedge work of medium vertices
     // scratch
@@ -210,6 +212,7 @@ cudaError_t run_node_sums(gd_graph *g);                                      // 
 size_t clique_big_bytes(int32_t dm);
 cudaError_t clique_pairs_bytes(gd_graph *g, const int32_t *counters_host, size_t *need);
 cudaError_t run_tri_bound(gd_graph *g, int64_t *total);
+cudaError_t run_hub_offsets(gd_graph *g, int32_t nh, int64_t *flat);
 int64_t medium_table_limit(int64_t nnz);
 size_t clique_pairs_bound(int sms, int64_t n);                                         // per CTA
 cudaError_t run_cycles(gd_graph *g, bool per_edge, const int32_t *counters_host);

@@ -67,43 +67,93 @@ __global__ void k_neighbor_degree(int64_t nnz, const int32_t *__restrict__ rp, c
 
 // Per vertex: wedge work, out-degree, tiers.  counters:
 //  [C_SMALL] [C_MEDIUM] [C_MAXDP] [C_HUB] [C_CL0..C_CL3] clique buckets
-__global__ void k_schedule(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
-                           const int32_t *__restrict__ nd, int64_t small_cap, int64_t hub_min, int32_t cl_max,
-                           int32_t *vlist, int32_t *hubs, int32_t *clist, int32_t *counters, int64_t *dplus,
-                           int64_t *west, int32_t *tlist) {
-    const int lane = lane_id();
-    for (int32_t u = global_warp(); u < n; u += num_warps()) {
-        const int32_t bu = rp[u], du = rp[u + 1] - bu;
-        int64_t est = 0;
-        int32_t dp = 0;
-        for (int32_t i = lane; i < du; i += WARP) {
-            const int32_t v = ci[bu + i], dv = nd[bu + i];
-            if (precedes(dv, v, du, u)) est += dv; else dp++;
-        }
-        est = warp_sum(est);
-        dp = warp_sum(dp);
-        if (lane == 0) {
-            dplus[u] = dp;
-            atomicMax(counters + C_MAXDP, dp);
-            if (est > 0) {
-                if (est <= TINY_WEDGES) tlist[atomicAdd(counters + C_TINY, 1)] = u;
-                else if (est <= small_cap) vlist[atomicAdd(counters + C_SMALL, 1)] = u;
-                else if (est <= hub_min) {
-                    vlist[n - 1 - atomicAdd(counters + C_MEDIUM, 1)] = u;
-                    atomicMax(reinterpret_cast<unsigned long long *>(west + n), (unsigned long long)est);
-                    west[u] = est;
-                    atomicAdd(counters + C_MB0 + min(MB_BUCKETS - 1, 63 - __clzll(est)), 1);
+// A CTA takes tiles of 256 vertices (a warp per vertex, 32 vertices per
+// warp); list positions are claimed in shared memory and each list's range
+// for the tile with one global atomic, so the few list counters are not
+// hammered by one atomic per vertex.
+constexpr int SCHED_TILE = 256;
+
+__global__ void __launch_bounds__(256)
+k_schedule(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+           const int32_t *__restrict__ nd, int64_t small_cap, int64_t hub_min, int32_t cl_max,
+           int32_t *vlist, int32_t *hubs, int32_t *clist, int32_t *counters, int64_t *dplus,
+           int64_t *west, int32_t *tlist) {
+    // lists: 0 tiny, 1 small, 2 medium, 3 hub, 4..7 clique buckets
+    __shared__ int32_t cnt[8], base[8];
+    __shared__ int32_t tile_maxdp;
+    __shared__ unsigned long long tile_maxw;
+    __shared__ int8_t code_l[SCHED_TILE], code_b[SCHED_TILE];
+    __shared__ int32_t pos_l[SCHED_TILE], pos_b[SCHED_TILE];
+    const int lane = lane_id(), warp = threadIdx.x >> 5;
+    for (int64_t t0 = (int64_t)blockIdx.x * SCHED_TILE; t0 < n; t0 += (int64_t)gridDim.x * SCHED_TILE) {
+        if (threadIdx.x < 8) cnt[threadIdx.x] = 0;
+        if (threadIdx.x == 0) { tile_maxdp = 0; tile_maxw = 0; }
+        __syncthreads();
+        for (int k = 0; k < 32; k++) {
+            const int t = warp * 32 + k;
+            const int64_t uu = t0 + t;
+            if (uu >= n) break;
+            const int32_t u = (int32_t)uu;
+            const int32_t bu = rp[u], du = rp[u + 1] - bu;
+            int64_t est = 0;
+            int32_t dp = 0;
+            for (int32_t i = lane; i < du; i += WARP) {
+                const int32_t v = ci[bu + i], dv = nd[bu + i];
+                if (precedes(dv, v, du, u)) est += dv; else dp++;
+            }
+            est = warp_sum(est);
+            dp = warp_sum(dp);
+            if (lane == 0) {
+                dplus[u] = dp;
+                atomicMax(&tile_maxdp, dp);
+                int l = -1;
+                if (est > 0) {
+                    if (est <= TINY_WEDGES) l = 0;
+                    else if (est <= small_cap) l = 1;
+                    else if (est <= hub_min) {
+                        l = 2;
+                        atomicMax(&tile_maxw, (unsigned long long)est);
+                        west[u] = est;
+                        atomicAdd(counters + C_MB0 + min(MB_BUCKETS - 1, 63 - __clzll(est)), 1);
+                    } else {
+                        l = 3;
+                    }
                 }
-                else hubs[atomicAdd(counters + C_HUB, 1)] = u;
-            }
-            // clique buckets by out-degree (a node needs 2 out-neighbours to
-            // be the lowest node of a triangle)
-            if (dp >= 2) {
-                const int bkt = (dp > cl_max || dp > CL_D2) ? 3 : dp <= CL_D0 ? 0 : dp <= CL_D1 ? 1 : 2;
-                const int32_t pos = atomicAdd(counters + C_CL0 + bkt, 1);
-                clist[(int64_t)bkt * n + pos] = u;
+                code_l[t] = (int8_t)l;
+                if (l >= 0) pos_l[t] = atomicAdd(&cnt[l], 1);
+                // clique buckets by out-degree (a node needs 2 out-neighbours to
+                // be the lowest node of a triangle)
+                int bkt = -1;
+                if (dp >= 2) {
+                    bkt = (dp > cl_max || dp > CL_D2) ? 3 : dp <= CL_D0 ? 0 : dp <= CL_D1 ? 1 : 2;
+                    pos_b[t] = atomicAdd(&cnt[4 + bkt], 1);
+                }
+                code_b[t] = (int8_t)bkt;
             }
         }
+        __syncthreads();
+        if (threadIdx.x < 8) {
+            const int l = threadIdx.x;
+            const int ctr = l == 0 ? C_TINY : l == 1 ? C_SMALL : l == 2 ? C_MEDIUM : l == 3 ? C_HUB : C_CL0 + (l - 4);
+            base[l] = cnt[l] ? atomicAdd(counters + ctr, cnt[l]) : 0;
+        }
+        if (threadIdx.x == 0) {
+            atomicMax(counters + C_MAXDP, tile_maxdp);
+            if (tile_maxw) atomicMax(reinterpret_cast<unsigned long long *>(west + n), tile_maxw);
+        }
+        __syncthreads();
+        const int t = threadIdx.x;
+        if (t0 + t < n) {
+            const int32_t u = (int32_t)(t0 + t);
+            const int l = code_l[t];
+            if (l == 0) tlist[base[0] + pos_l[t]] = u;
+            else if (l == 1) vlist[base[1] + pos_l[t]] = u;
+            else if (l == 2) vlist[n - 1 - (base[2] + pos_l[t])] = u;
+            else if (l == 3) hubs[base[3] + pos_l[t]] = u;
+            const int bk = code_b[t];
+            if (bk >= 0) clist[(int64_t)bk * n + base[4 + bk] + pos_b[t]] = u;
+        }
+        __syncthreads();
     }
 }
 
@@ -1051,28 +1101,31 @@ k_cycles_medium(CycleArgs a) {
     }
 }
 
-// Hub tier preparation: offsets of the batch's hub rows in one flat list.
-__global__ void k_hub_offsets(CycleArgs a) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    int64_t o = 0;
-    for (int h = 0; h < a.nhub; h++) {
-        a.hoff[h] = o;
-        const int32_t u = a.hubs[a.hub0 + h];
-        o += a.rp[u + 1] - a.rp[u];
+// Hub tier preparation, once for all hubs: hoff = exclusive prefix of the
+// hubs' degrees (the hubs' rows concatenated form one flat list), hlen[j] =
+// wedges of flat neighbour j (d_v if v ranks below its hub, else 0), and
+// its exclusive prefix hpre (hpre[F] = all hub wedges).  A batch of hubs
+// [hub0, hub0 + nhub) owns flat [hoff[hub0], hoff[hub0 + nhub]).
+__global__ void k_hub_degrees(int32_t nh, const int32_t *__restrict__ hubs, const int32_t *__restrict__ rp,
+                              int64_t *deg) {
+    for (int32_t h = blockIdx.x * blockDim.x + threadIdx.x; h < nh; h += gridDim.x * blockDim.x) {
+        const int32_t u = hubs[h];
+        deg[h] = rp[u + 1] - rp[u];
     }
-    a.hoff[a.nhub] = o;
 }
 
-// Wedges contributed by each neighbour of each hub of the batch: d_v if v
-// ranks below its hub, else 0.
-__global__ void k_hub_lengths(CycleArgs a) {
-    const int64_t total = a.hoff[a.nhub];
+__global__ void k_hub_lengths(CycleArgs a, int32_t nh) {
+    const int64_t total = a.hoff[nh];
     for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < total; j += (int64_t)gridDim.x * blockDim.x) {
-        int h = 0;
-        while (h + 1 < a.nhub && a.hoff[h + 1] <= j) h++;
-        const int32_t u = a.hubs[a.hub0 + h];
+        // hub of flat entry j: the last h with hoff[h] <= j
+        int32_t lo = 0, hi = nh - 1;
+        while (lo < hi) {
+            const int32_t mid = (lo + hi + 1) >> 1;
+            if (a.hoff[mid] <= j) lo = mid; else hi = mid - 1;
+        }
+        const int32_t u = a.hubs[lo];
         const int32_t bu = a.rp[u], du = a.rp[u + 1] - bu;
-        const int32_t i = (int32_t)(j - a.hoff[h]);
+        const int32_t i = (int32_t)(j - a.hoff[lo]);
         const int32_t v = a.ci[bu + i], dv = a.nd[bu + i];
         a.hlen[j] = precedes(dv, v, du, u) ? dv : 0;
     }
@@ -1085,22 +1138,23 @@ __global__ void k_hub_lengths(CycleArgs a) {
 // time, clipping the lists that straddle the range ends.  Hub h counts into
 // table h.
 template <int PH>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 8)
 k_cycles_hub(CycleArgs a) {
     __shared__ unsigned long long item[8][WARP];
     const int lane = lane_id(), warp = threadIdx.x >> 5;
     item[warp][lane] = 0;
     __syncwarp();
-    const int64_t flat = a.hoff[a.nhub];
-    const int64_t wtot = a.hpre[flat];
+    const int64_t *hoff = a.hoff + a.hub0;          // the batch's rows in the flat list
+    const int64_t f0 = hoff[0], flat = hoff[a.nhub];
+    const int64_t wbase = a.hpre[f0], wtot = a.hpre[flat] - wbase;
     // every warp of the grid takes an equal share of the batch's wedges
     const int64_t gw = global_warp(), gwn = num_warps();
     {
-        const int64_t w_lo = wtot * gw / gwn;
-        const int64_t w_hi = wtot * (gw + 1) / gwn;
+        const int64_t w_lo = wbase + wtot * gw / gwn;
+        const int64_t w_hi = wbase + wtot * (gw + 1) / gwn;
         if (w_lo >= w_hi) return;
-        // largest j with hpre[j] <= w_lo
-        int64_t lo = 0, hi = flat;
+        // largest j in [f0, flat) with hpre[j] <= w_lo
+        int64_t lo = f0, hi = flat;
         while (lo < hi) {
             const int64_t mid = (lo + hi + 1) >> 1;
             if (a.hpre[mid] <= w_lo) lo = mid; else hi = mid - 1;
@@ -1113,11 +1167,11 @@ k_cycles_hub(CycleArgs a) {
                 const int64_t p0 = a.hpre[j], p1 = a.hpre[j + 1];
                 const int64_t s0 = max(p0, w_lo), e0 = min(p1, w_hi);
                 if (e0 > s0) {
-                    while (h + 1 < a.nhub && a.hoff[h + 1] <= j) h++;
+                    while (h + 1 < a.nhub && hoff[h + 1] <= j) h++;
                     u = a.hubs[a.hub0 + h];
                     const int32_t bu = a.rp[u];
                     du = a.rp[u + 1] - bu;
-                    slot_uv = bu + (int32_t)(j - a.hoff[h]);
+                    slot_uv = bu + (int32_t)(j - hoff[h]);
                     const int32_t v = a.ci[slot_uv];
                     len = (int32_t)(e0 - s0);
                     start = a.rp[v] + (int32_t)(s0 - p0);
@@ -1238,7 +1292,7 @@ cudaError_t run_schedule(gd_graph *g, int32_t *counters_host) {
         GD_LAUNCH(g, "k_neighbor_degree", k_neighbor_degree, grid_for(g->nnz, 256, sms * 16), 256, 0,
                   g->nnz, g->rp, g->ci, w.nd);
         const int64_t small_cap = g->ctx->opt.smem_table_max / 2;
-        GD_LAUNCH(g, "k_schedule", k_schedule, grid_for((int64_t)n * 32, 256, sms * 16), 256, 0,
+        GD_LAUNCH(g, "k_schedule", k_schedule, grid_for(n, SCHED_TILE, sms * 8), 256, 0,
                   n, g->rp, g->ci, w.nd, small_cap, (int64_t)1 << g->ctx->opt.hub_wedges_log2,
                   g->ctx->opt.bitmap_max_outdeg, w.vlist, w.hubs, w.clist, w.counters, w.scan_tmp, w.west,
                   w.tlist);
@@ -1351,6 +1405,21 @@ cudaError_t clique_pairs_bytes(gd_graph *g, const int32_t *cnt, size_t *need) {
     return pairs_need<CL_D2, 512, false>(g, cnt[C_CL0 + 2], need);
 }
 
+// Flat row offsets of all hubs (hub_off, nh + 1 entries); *flat receives
+// hub_off[nh], the length of the hubs' concatenated rows.
+cudaError_t run_hub_offsets(gd_graph *g, int32_t nh, int64_t *flat) {
+    Workspace &w = g->ws;
+    *flat = 0;
+    if (nh == 0) return cudaSuccess;
+    GD_LAUNCH(g, "k_hub_degrees", k_hub_degrees, grid_for(nh, 256, sms_of(g) * 4), 256, 0, nh, w.hubs, g->rp,
+              w.scan_tmp);
+    cudaError_t e = exclusive_scan_i64(g, w.scan_tmp, w.hub_off, nh, w.scan_tmp + (nh + 1));
+    if (e) return e;
+    e = cudaMemcpyAsync(flat, w.hub_off + nh, sizeof(int64_t), cudaMemcpyDeviceToHost, g->stream);
+    if (e) return e;
+    return cudaStreamSynchronize(g->stream);
+}
+
 // Offsets of the per-node triangle record regions (toff, n + 1 entries);
 // *total receives toff[n].
 cudaError_t run_tri_bound(gd_graph *g, int64_t *total) {
@@ -1436,20 +1505,17 @@ cudaError_t run_cycles(gd_graph *g, bool per_edge, const int32_t *cnt) {
     a.tables = w.wtab; a.mtab = w.mtab; a.mcap = w.mtab_cap; a.west = w.west; a.status = w.status;
     a.yacc = (unsigned long long *)w.yacc; a.sums = w.sums;
     a.hub0 = 0; a.nhub = 0;
-    // hubs, in batches
+    // hubs, in batches, over one flat wedge prefix of all hubs
     const int32_t nh = cnt[C_HUB], B = hub_batch(g);
     a.hoff = w.hub_off; a.hlen = w.hub_len; a.hpre = w.hub_pre;
+    if (nh > 0) {
+        GD_LAUNCH(g, "k_hub_lengths", k_hub_lengths, grid_for(w.hub_flat, 256, sms * 8), 256, 0, a, nh);
+        e = exclusive_scan_i64(g, w.hub_len, w.hub_pre, w.hub_flat, w.hub_scan_tmp);
+        if (e) return e;
+    }
     for (int32_t h0 = 0; h0 < nh; h0 += B) {
         a.hub0 = h0;
         a.nhub = nh - h0 < B ? nh - h0 : B;
-        GD_LAUNCH(g, "k_hub_offsets", k_hub_offsets, 1, 32, 0, a);
-        // lengths beyond the batch's flat list stay 0, so one scan over the
-        // capacity gives the prefix (and the total at every index >= flat)
-        e = cudaMemsetAsync(w.hub_len, 0, sizeof(int64_t) * (size_t)w.hub_flat_cap, g->stream);
-        if (e) return e;
-        GD_LAUNCH(g, "k_hub_lengths", k_hub_lengths, (unsigned)(sms * 4), 256, 0, a);
-        e = exclusive_scan_i64(g, w.hub_len, w.hub_pre, w.hub_flat_cap, w.hub_scan_tmp);
-        if (e) return e;
         GD_LAUNCH(g, "k_cycles_hub_count", k_cycles_hub<0>, (unsigned)(sms * 8), 256, 0, a);
         if (per_edge) GD_LAUNCH(g, "k_cycles_hub_credit", k_cycles_hub<1>, (unsigned)(sms * 8), 256, 0, a);
         if (per_edge) GD_LAUNCH(g, "k_cycles_hub_clear", k_cycles_hub_clear<true>, (unsigned)(sms * 4), 256, 0, a);
