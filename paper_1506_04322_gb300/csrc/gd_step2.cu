@@ -445,9 +445,13 @@ k_clique_bitmap(CliqueArgs a) {
     const int32_t *list = a.clist + (int64_t)a.bucket * a.n;
     unsigned long long k4_local = 0;   // 3 x 4-cliques (COUNT)
 
-    int32_t idx = take(tt == 0 ? atomicAdd(a.dyn, 1) : 0);
+    // warp teams claim CH consecutive list positions per atomic (one counter
+    // for ~a million small nodes would serialise on it); CTA teams one
+    constexpr int32_t CH = WARP_TEAMS ? 8 : 1;
+    int32_t cbase = take(tt == 0 ? atomicAdd(a.dyn, CH) : 0), cnext = 0;
+    int32_t idx = cbase;
     while (idx < nv) {
-        const int32_t pending = tt == 0 ? atomicAdd(a.dyn, 1) : 0;   // the team's next node
+        if (idx == cbase) cnext = take(tt == 0 ? atomicAdd(a.dyn, CH) : 0);   // the team's next chunk
         const int32_t va = list[idx];
         const int32_t off = a.dag_off[va], D = a.dag_off[va + 1] - off;
         const int32_t Wd = (D + 31) >> 5;
@@ -626,7 +630,7 @@ k_clique_bitmap(CliqueArgs a) {
             }
         }
         team_sync();
-        idx = take(pending);
+        if (++idx == cbase + CH) { cbase = cnext; idx = cbase; }
     }
     if (MODE == MODE_COUNT) {
         __shared__ unsigned long long red[NW];
