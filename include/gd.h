@@ -118,7 +118,7 @@ typedef struct gd_options {
     int32_t hub_wedges_log2;  /* vertices with more than 2^k wedges are processed
                                  by the whole GPU in batches; below, one CTA per
                                  vertex with a table of up to 2^(k+1) entries
-                                 (default 18)                                   */
+                                 (default 17)                                   */
     int32_t reserved[6];
 } gd_options;
 

@@ -249,7 +249,7 @@ size_t estimate_footprint(gd_ctx *ctx, int64_t n, int64_t nnz, bool per_edge, bo
     if (n > 0) {
         // medium-tier tables: W(u) <= min(2^hub, nnz) entries, two per SM,
         // within the per-graph limit
-        const int64_t hub = int64_t(1) << (ctx ? ctx->opt.hub_wedges_log2 : 18);
+        const int64_t hub = int64_t(1) << (ctx ? ctx->opt.hub_wedges_log2 : 17);
         int64_t cap = 1024;
         while (cap < 2 * std::min<int64_t>(hub, nnz)) cap <<= 1;
         const int64_t ctas = std::min<int64_t>(2 * (ctx ? ctx->num_sms : 152), n);
@@ -476,7 +476,7 @@ void gd_default_options(gd_options *opt) {
     opt->ctas_per_sm = 0;
     opt->smem_table_max = 8192;
     opt->bitmap_max_outdeg = gdi::CL_D2;
-    opt->hub_wedges_log2 = 18;
+    opt->hub_wedges_log2 = 17;
 }
 
 static int check_options(gd_options *o) {
@@ -484,7 +484,7 @@ static int check_options(gd_options *o) {
     if (t < 256 || t > 16384 || (t & (t - 1))) return GD_EINVAL;
     if (o->variant < 0 || o->variant > 2) return GD_EINVAL;
     if (o->bitmap_max_outdeg == 0) o->bitmap_max_outdeg = gdi::CL_D2;
-    if (o->hub_wedges_log2 == 0) o->hub_wedges_log2 = 18;
+    if (o->hub_wedges_log2 == 0) o->hub_wedges_log2 = 17;
     if (o->bitmap_max_outdeg < 2 || o->bitmap_max_outdeg > gdi::CL_D2 || o->hub_wedges_log2 < 4 ||
         o->hub_wedges_log2 > 40) return GD_EINVAL;
     return GD_OK;

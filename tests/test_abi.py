@@ -40,7 +40,7 @@ def test_options_layout_and_defaults(lib):
     assert o.variant == gd.GD_VARIANT_AUTO
     assert o.smem_table_max >= 256 and (o.smem_table_max & (o.smem_table_max - 1)) == 0
     assert ctypes.sizeof(gd.gd_options) == 48
-    assert o.bitmap_max_outdeg == 1024 and o.hub_wedges_log2 == 18
+    assert o.bitmap_max_outdeg == 1024 and o.hub_wedges_log2 == 17
 
 
 def test_generators_are_deterministic_and_simple():
