@@ -53,7 +53,6 @@ constexpr int MB_BUCKETS = 40;
 constexpr int TINY_WEDGES = 256;   // warp-level wedge table of 2 * TINY_WEDGES entries
 constexpr int CL_D0 = 64, CL_D1 = 256, CL_D2 = 1024;
 constexpr int CL_BIG_THREADS = 512;   // CTA size of the large out-list (global scratch) variant
-constexpr long long HUB_MIN_WEDGES = 1ll << 18;
 
 // Device-side error bits (gdi::Status word).
 enum ErrBits {
