@@ -778,6 +778,97 @@ struct CycleArgs {
 
 __device__ __forceinline__ unsigned long long c2(uint32_t c) { return (unsigned long long)c * (c - 1) / 2; }
 
+// Wedge prefix over N(u) in shared memory: pre[i] = wedges of the
+// neighbours before i (d_v for v below u, else 0), pre[du] = W(u).  All
+// threads of the CTA call it; wsum holds THREADS / 32 entries.
+template <int THREADS>
+__device__ __forceinline__ long long wedge_prefix(const CycleArgs &a, int32_t u, int32_t bu, int32_t du,
+                                                  long long *pre, long long *wsum) {
+    constexpr int NW = THREADS / 32;
+    const int lane = lane_id(), warp = threadIdx.x >> 5;
+    long long carry = 0;
+    for (int32_t b0 = 0; b0 < du; b0 += THREADS) {
+        const int32_t i = b0 + threadIdx.x;
+        long long len = 0;
+        if (i < du) {
+            const int32_t v = a.ci[bu + i], dv = a.nd[bu + i];
+            if (precedes(dv, v, du, u)) len = dv;
+        }
+        long long incl = len;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const long long y = __shfl_up_sync(FULL, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (lane == 31) wsum[warp] = incl;
+        __syncthreads();
+        long long before = 0, all = 0;
+        for (int j = 0; j < NW; j++) { const long long t = wsum[j]; before += j < warp ? t : 0; all += t; }
+        if (i < du) pre[i] = carry + before + incl - len;
+        carry += all;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) pre[du] = carry;
+    __syncthreads();
+    return carry;
+}
+
+// The wedges [w_lo, w_hi) of vertex u (flat over N(u) by the prefix pre):
+// neighbours 32 at a time, their lists clipped to the range and spread over
+// the lanes.  f(k, q, y, ok, live) per wedge slot as in warp_wedges;
+// flush(j) after each group of 32 neighbours, j = the lane's neighbour.
+template <typename F, typename G>
+__device__ __forceinline__ void walk_range(const CycleArgs &a, int32_t u, int32_t bu, int32_t du,
+                                           const long long *pre, long long w_lo, long long w_hi, F f, G flush) {
+    if (w_lo >= w_hi) return;
+    const int lane = lane_id();
+    int32_t lo = 0, hi = du;
+    while (lo < hi) {
+        const int32_t mid = (lo + hi + 1) >> 1;
+        if (pre[mid] <= w_lo) lo = mid; else hi = mid - 1;
+    }
+    for (int32_t j0 = lo; j0 < du && pre[j0] < w_hi; j0 += WARP) {
+        const int32_t j = j0 + lane;
+        int32_t len = 0, start = 0;
+        if (j < du) {
+            const long long p0 = pre[j], p1 = pre[j + 1];
+            const long long s0 = max(p0, w_lo), e0 = min(p1, w_hi);
+            if (e0 > s0) {
+                len = (int32_t)(e0 - s0);
+                start = a.rp[a.ci[bu + j]] + (int32_t)(s0 - p0);
+            }
+        }
+        const int32_t incl = warp_incl_scan(len);
+        const int32_t total = __shfl_sync(FULL, incl, 31);
+        const int32_t excl = incl - len;
+        for (int32_t w0 = 0; w0 < total; w0 += WARP) {
+            const int32_t w = w0 + lane;
+            int32_t k = 0;
+#pragma unroll
+            for (int s = 16; s >= 1; s >>= 1) {
+                const int32_t e = __shfl_sync(FULL, excl, k + s);
+                if (e <= w) k += s;
+            }
+            const int32_t ks = __shfl_sync(FULL, start, k);
+            const int32_t ke = __shfl_sync(FULL, excl, k);
+            const bool live = w < total;
+            bool ok = false;
+            int32_t q = 0, y = 0;
+            if (live) {
+                q = ks + (w - ke);
+                y = a.ci[q];
+                ok = precedes(a.nd[q], y, du, u);
+            }
+            f(k, q, y, ok, live);
+        }
+        flush(j);
+    }
+}
+
+// Wedge prefix of the small tier in shared memory: vertices of larger
+// degree walk their neighbours 32 at a time per warp instead.
+constexpr int SMALL_PCAP = 2048;
+
 // Tiny tier: one warp per vertex (at most TINY_WEDGES wedges), each warp
 // with its own shared-memory hash of 2 * TINY_WEDGES entries; no CTA barriers.
 template <bool CREDIT>
@@ -857,9 +948,12 @@ k_cycles_small(CycleArgs a) {
     extern __shared__ __align__(16) int32_t sm[];
     __shared__ int32_t ntouched;
     __shared__ unsigned long long item[NW][WARP];
-    int32_t *keys = sm;
-    uint32_t *vals = (uint32_t *)(sm + (a.capmask + 1));
-    int32_t *touched = sm + 2 * (a.capmask + 1);
+    __shared__ long long wsum[NW];
+    // wedge prefix (SMALL_PCAP + 1 entries), then the hash keys, counts and touched slots
+    long long *pre = reinterpret_cast<long long *>(sm);
+    int32_t *keys = sm + 2 * (SMALL_PCAP + 1);
+    uint32_t *vals = (uint32_t *)(keys + (a.capmask + 1));
+    int32_t *touched = keys + 2 * (a.capmask + 1);
     const int lane = lane_id(), warp = threadIdx.x >> 5;
     const int32_t nv = a.counters[C_SMALL];
     for (uint32_t i = threadIdx.x; i <= a.capmask; i += THREADS) { keys[i] = -1; vals[i] = 0; }
@@ -870,39 +964,55 @@ k_cycles_small(CycleArgs a) {
     for (int32_t idx = blockIdx.x; idx < nv; idx += gridDim.x) {
         const int32_t u = a.vlist[idx];
         const int32_t bu = a.rp[u], du = a.rp[u + 1] - bu;
-        warp_wedges(u, du, bu, warp * WARP, du, NW * WARP, a.rp, a.ci, a.nd,
-            [&](int k, int32_t q, int32_t y, bool ok, bool live) {
-                if (!ok) return;
-                uint32_t h = hash32((uint32_t)y) & a.capmask;
-                uint32_t old = 0;
-                while (true) {
-                    const int32_t kk = keys[h];
-                    if (kk == y) { old = atomicAdd(vals + h, 1u); break; }
-                    if (kk == -1) {
-                        const int32_t prev = atomicCAS(keys + h, -1, y);
-                        if (prev == -1) { old = atomicAdd(vals + h, 1u); touched[atomicAdd(&ntouched, 1)] = (int32_t)h; break; }
-                        if (prev == y) { old = atomicAdd(vals + h, 1u); break; }
-                    }
-                    h = (h + 1) & a.capmask;
+        auto count = [&](int k, int32_t q, int32_t y, bool ok, bool live) {
+            if (!ok) return;
+            uint32_t h = hash32((uint32_t)y) & a.capmask;
+            uint32_t old = 0;
+            for (uint32_t probe = 0; probe <= a.capmask; probe++) {
+                const int32_t kk = keys[h];
+                if (kk == y) { old = atomicAdd(vals + h, 1u); break; }
+                if (kk == -1) {
+                    const int32_t prev = atomicCAS(keys + h, -1, y);
+                    if (prev == -1) { old = atomicAdd(vals + h, 1u); touched[atomicAdd(&ntouched, 1)] = (int32_t)h; break; }
+                    if (prev == y) { old = atomicAdd(vals + h, 1u); break; }
                 }
-                if (!CREDIT) c4 += old;
-            },
-            [&](int32_t) {});
-        __syncthreads();
-        if (CREDIT) {
-            warp_wedges(u, du, bu, warp * WARP, du, NW * WARP, a.rp, a.ci, a.nd,
-                [&](int k, int32_t q, int32_t y, bool ok, bool live) {
-                    const uint32_t c = ok ? sm_find(keys, vals, a.capmask, y) : 0;
-                    if (c > 1) atomicAdd(a.yacc + q, (unsigned long long)(c - 1));
-                    item_add(item[warp], k, c > 1 ? c - 1 : 0, live);
-                },
-                [&](int32_t it) {
+                h = (h + 1) & a.capmask;
+            }
+            if (!CREDIT) c4 += old;
+        };
+        auto credit = [&](int k, int32_t q, int32_t y, bool ok, bool live) {
+            const uint32_t c = ok ? sm_find(keys, vals, a.capmask, y) : 0;
+            if (c > 1) atomicAdd(a.yacc + q, (unsigned long long)(c - 1));
+            item_add(item[warp], k, c > 1 ? c - 1 : 0, live);
+        };
+        if (du <= SMALL_PCAP) {
+            // every warp takes an equal range of the vertex's wedges
+            const long long W = wedge_prefix<THREADS>(a, u, bu, du, pre, wsum);
+            const long long w_lo = W * warp / NW, w_hi = W * (warp + 1) / NW;
+            walk_range(a, u, bu, du, pre, w_lo, w_hi, count, [&](int32_t) {});
+            __syncthreads();
+            if (CREDIT) {
+                walk_range(a, u, bu, du, pre, w_lo, w_hi, credit, [&](int32_t j) {
                     __syncwarp();
-                    const unsigned long long s = item[warp][lane];
-                    if (s) { atomicAdd(a.yacc + bu + it + lane, s); item[warp][lane] = 0; }
+                    const unsigned long long sv = item[warp][lane];
+                    if (sv) { atomicAdd(a.yacc + bu + j, sv); item[warp][lane] = 0; }
                     __syncwarp();
                 });
+                __syncthreads();
+            }
+        } else {
+            warp_wedges(u, du, bu, warp * WARP, du, NW * WARP, a.rp, a.ci, a.nd, count, [&](int32_t) {});
             __syncthreads();
+            if (CREDIT) {
+                warp_wedges(u, du, bu, warp * WARP, du, NW * WARP, a.rp, a.ci, a.nd, credit,
+                    [&](int32_t it) {
+                        __syncwarp();
+                        const unsigned long long sv = item[warp][lane];
+                        if (sv) { atomicAdd(a.yacc + bu + it + lane, sv); item[warp][lane] = 0; }
+                        __syncwarp();
+                    });
+                __syncthreads();
+            }
         }
         const int32_t nt = ntouched;
         for (int32_t i = threadIdx.x; i < nt; i += THREADS) {
@@ -997,84 +1107,19 @@ k_cycles_medium(CycleArgs a) {
             item_add(item[warp], k, c > 1 ? c - 1 : 0, live);
         };
         if (du <= MED_PCAP) {
-            // prefix of the wedge counts over N(u) (d_v for v below u)
-            long long carry = 0;
-            for (int32_t b0 = 0; b0 < du; b0 += THREADS) {
-                const int32_t i = b0 + threadIdx.x;
-                long long len = 0;
-                if (i < du) {
-                    const int32_t v = a.ci[bu + i], dv = a.nd[bu + i];
-                    if (precedes(dv, v, du, u)) len = dv;
-                }
-                long long incl = len;
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const long long y = __shfl_up_sync(FULL, incl, o);
-                    if (lane >= o) incl += y;
-                }
-                if (lane == 31) wsum[warp] = incl;
-                __syncthreads();
-                long long before = 0, all = 0;
-                for (int j = 0; j < NW; j++) { const long long t = wsum[j]; before += j < warp ? t : 0; all += t; }
-                if (i < du) pre[i] = carry + before + incl - len;
-                carry += all;
-                __syncthreads();
-            }
-            if (threadIdx.x == 0) pre[du] = carry;
-            __syncthreads();
-            const long long W = carry;
-            // every warp takes an equal range of the wedges
+            // every warp takes an equal range of the vertex's wedges
+            const long long W = wedge_prefix<THREADS>(a, u, bu, du, pre, wsum);
             for (int ph = 0; ph < (CREDIT ? 2 : 1); ph++) {
                 const long long w_lo = W * warp / NW, w_hi = W * (warp + 1) / NW;
-                if (w_lo < w_hi) {
-                    int32_t lo = 0, hi = du;
-                    while (lo < hi) {
-                        const int32_t mid = (lo + hi + 1) >> 1;
-                        if (pre[mid] <= w_lo) lo = mid; else hi = mid - 1;
-                    }
-                    for (int32_t j0 = lo; j0 < du && pre[j0] < w_hi; j0 += WARP) {
-                        // lane l: neighbour j0 + l, its wedges clipped to [w_lo, w_hi)
-                        const int32_t j = j0 + lane;
-                        int32_t len = 0, start = 0;
-                        if (j < du) {
-                            const long long p0 = pre[j], p1 = pre[j + 1];
-                            const long long s0 = max(p0, w_lo), e0 = min(p1, w_hi);
-                            if (e0 > s0) {
-                                len = (int32_t)(e0 - s0);
-                                start = a.rp[a.ci[bu + j]] + (int32_t)(s0 - p0);
-                            }
-                        }
-                        const int32_t incl = warp_incl_scan(len);
-                        const int32_t total = __shfl_sync(FULL, incl, 31);
-                        const int32_t excl = incl - len;
-                        for (int32_t w0 = 0; w0 < total; w0 += WARP) {
-                            const int32_t w = w0 + lane;
-                            int32_t k = 0;
-#pragma unroll
-                            for (int s = 16; s >= 1; s >>= 1) {
-                                const int32_t e = __shfl_sync(FULL, excl, k + s);
-                                if (e <= w) k += s;
-                            }
-                            const int32_t ks = __shfl_sync(FULL, start, k);
-                            const int32_t ke = __shfl_sync(FULL, excl, k);
-                            const bool live = w < total;
-                            bool ok = false;
-                            int32_t q = 0, y = 0;
-                            if (live) {
-                                q = ks + (w - ke);
-                                y = a.ci[q];
-                                ok = precedes(a.nd[q], y, du, u);
-                            }
-                            if (ph == 0) count(k, q, y, ok, live);
-                            else credit(k, q, y, ok, live);
-                        }
-                        if (ph == 1) {
-                            __syncwarp();
-                            const unsigned long long sv = item[warp][lane];
-                            if (sv) { atomicAdd(a.yacc + bu + j, sv); item[warp][lane] = 0; }
-                            __syncwarp();
-                        }
-                    }
+                if (ph == 0) {
+                    walk_range(a, u, bu, du, pre, w_lo, w_hi, count, [&](int32_t) {});
+                } else {
+                    walk_range(a, u, bu, du, pre, w_lo, w_hi, credit, [&](int32_t j) {
+                        __syncwarp();
+                        const unsigned long long sv = item[warp][lane];
+                        if (sv) { atomicAdd(a.yacc + bu + j, sv); item[warp][lane] = 0; }
+                        __syncwarp();
+                    });
                 }
                 __syncthreads();
             }
@@ -1545,7 +1590,7 @@ cudaError_t run_cycles(gd_graph *g, bool per_edge, const int32_t *cnt) {
     }
     // small tier
     if (cnt[C_SMALL] > 0) {
-        const size_t smem = (size_t)(a.capmask + 1) * 8 + (size_t)((a.capmask + 1) / 2) * 4;
+        const size_t smem = (size_t)(SMALL_PCAP + 1) * 8 + (size_t)(a.capmask + 1) * 8 + (size_t)((a.capmask + 1) / 2) * 4;
         if (per_edge) {
             if ((e = allow_smem(k_cycles_small<256, true>, smem))) return e;
             GD_LAUNCH(g, "k_cycles_small", (k_cycles_small<256, true>), (unsigned)(sms * 2), 256, smem, a);
