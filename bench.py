@@ -58,8 +58,9 @@ def parse():
     ap.add_argument("--global-only", action="store_true", help="time gd_count_global instead")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-graphs measurement")
     ap.add_argument("--no-serving", action="store_true", help="skip the request-loop measurement")
-    ap.add_argument("--workload", default="chung_lu_1m", choices=["chung_lu_1m", "chung_lu_400k"],
-                    help="chung_lu_400k: a 4M-edge graph of the same family, for profiler captures")
+    ap.add_argument("--workload", default="chung_lu_1m", choices=["chung_lu_1m", "chung_lu_400k", "rmat_22"],
+                    help="chung_lu_400k: a 4M-edge graph of the same family, for profiler captures; "
+                         "rmat_22: the R-MAT scale-22 graph (use with --global-only)")
     return ap.parse_args()
 
 
@@ -494,6 +495,8 @@ def run_gd(args):
     if args.workload == "chung_lu_400k":
         g = inputs.chung_lu(400_000, 2.1, 4_400_000, 20_000.0, 9)
         g.name = "chung_lu_n400k_gamma2.1_cap20k"
+    elif args.workload == "rmat_22":
+        g = inputs.rmat_22()           # the global counts (per-edge output would be 7.7 GB)
     else:
         g = inputs.chung_lu_1m()
     m = g.m
@@ -503,7 +506,7 @@ def run_gd(args):
     stream = torch.cuda.Stream(device=device)
     rp = torch.from_numpy(g.row_ptr).to(device)
     ci = torch.from_numpy(g.col_idx).to(device)
-    out = torch.empty((m, 15), dtype=torch.int64, device=device)
+    out = None if args.global_only else torch.empty((m, 15), dtype=torch.int64, device=device)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=device)
     torch.cuda.synchronize()
     h = ctx.graph(rp, ci, n=g.n, borrow=True, stream=stream.cuda_stream)
@@ -555,14 +558,17 @@ def run_gd(args):
     # end to end through the C ABI with pinned host buffers
     rp_h = torch.from_numpy(g.row_ptr).pin_memory()
     ci_h = torch.from_numpy(g.col_idx).pin_memory()
-    out_h = torch.empty((m, 15), dtype=torch.int64).pin_memory()
+    out_h = None if args.global_only else torch.empty((m, 15), dtype=torch.int64).pin_memory()
     h2d = 4 * (g.n + 1) + 4 * g.nnz
-    d2h = 8 * 15 * m + 16 * 15
+    d2h = (0 if args.global_only else 8 * 15 * m) + 16 * 15
 
     def e2e_step():
         gh = gd.gd_create_csr(ctx.handle, g.n, g.nnz, rp_h.data_ptr(), ci_h.data_ptr(), 0, stream.cuda_stream)
         try:
-            r = gd.gd_count_per_edge(ctx.handle, gh, out_h.data_ptr(), 0, True)
+            if args.global_only:
+                r = gd.gd_count_global(ctx.handle, gh)
+            else:
+                r = gd.gd_count_per_edge(ctx.handle, gh, out_h.data_ptr(), 0, True)
         finally:
             gd.gd_destroy_graph(gh)
         return r
@@ -623,7 +629,8 @@ def run_gd(args):
         "vs_baseline": None, "dtype": "u64", "data": "synthetic",
         "config": {"workload": g.name, "n": g.n, "m": g.m,
                    "mode": "global" if args.global_only else "per-edge (15 columns) + global",
-                   "variant": "oriented", "seed": 2, "l2": "flushed between timed steps (512 MB write)",
+                   "variant": "oriented", "seed": {"chung_lu_1m": 2, "chung_lu_400k": 9, "rmat_22": 3}[args.workload],
+                   "l2": "flushed between timed steps (512 MB write)",
                    "parallelism": f"replicas x{ws}"},
         "e2e": {"value": job_rate(m, ws, e2e_s), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
