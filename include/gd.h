@@ -115,10 +115,10 @@ typedef struct gd_options {
                                     arrays in shared memory; nodes with more use
                                     the same kernel on global scratch
                                     (default and maximum 1024, minimum 2)       */
-    int32_t hub_wedges_log2;  /* vertices with more than 2^k wedges are processed
-                                 by the whole GPU in batches; below, one CTA per
-                                 vertex with a table of up to 2^(k+1) entries
-                                 (default 17)                                   */
+    int32_t hub_wedges_log2;  /* vertices with more than max(2^k, n/8) wedges are
+                                 processed by the whole GPU in batches (dense
+                                 tables of n counters); below, one CTA per vertex
+                                 with a table sized to its wedges (default 17) */
     int32_t reserved[6];
 } gd_options;
 

@@ -249,7 +249,7 @@ size_t estimate_footprint(gd_ctx *ctx, int64_t n, int64_t nnz, bool per_edge, bo
     if (n > 0) {
         // medium-tier tables: W(u) <= min(2^hub, nnz) entries, two per SM,
         // within the per-graph limit
-        const int64_t hub = int64_t(1) << (ctx ? ctx->opt.hub_wedges_log2 : 17);
+        const int64_t hub = std::max<int64_t>(int64_t(1) << (ctx ? ctx->opt.hub_wedges_log2 : 17), n / 8);
         int64_t cap = 1024;
         while (cap < 2 * std::min<int64_t>(hub, nnz)) cap <<= 1;
         const int64_t ctas = std::min<int64_t>(2 * (ctx ? ctx->num_sms : 152), n);

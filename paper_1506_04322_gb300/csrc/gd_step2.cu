@@ -1341,8 +1341,11 @@ cudaError_t run_schedule(gd_graph *g, int32_t *counters_host) {
         GD_LAUNCH(g, "k_neighbor_degree", k_neighbor_degree, grid_for(g->nnz, 256, sms * 16), 256, 0,
                   g->nnz, g->rp, g->ci, w.nd);
         const int64_t small_cap = g->ctx->opt.smem_table_max / 2;
+        // a hub's dense table costs 4n bytes: below W = n/8 wedges the
+        // per-vertex open-addressing tables of the medium tier are cheaper
+        const int64_t hub_min = std::max<int64_t>((int64_t)1 << g->ctx->opt.hub_wedges_log2, (int64_t)n / 8);
         GD_LAUNCH(g, "k_schedule", k_schedule, grid_for(n, SCHED_TILE, sms * 8), 256, 0,
-                  n, g->rp, g->ci, w.nd, small_cap, (int64_t)1 << g->ctx->opt.hub_wedges_log2,
+                  n, g->rp, g->ci, w.nd, small_cap, hub_min,
                   g->ctx->opt.bitmap_max_outdeg, w.vlist, w.hubs, w.clist, w.counters, w.scan_tmp, w.west,
                   w.tlist);
         GD_LAUNCH(g, "k_medium_offsets", k_medium_offsets, 1, 32, 0, w.counters);
