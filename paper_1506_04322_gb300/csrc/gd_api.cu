@@ -625,6 +625,9 @@ int gd_create_csr(gd_ctx *ctx, int32_t n, int64_t nnz, const int32_t *row_ptr, c
         if (e != cudaSuccess) { rc = cuda_fail(ctx, e, "validate"); gd_destroy_graph(g); return rc; }
         if (bad_code) {
             gd_destroy_graph(g);
+            if (bad_index < 0)
+                return fail(ctx, GD_EINVAL, "invalid CSR: some entry below the diagonal has no reverse entry "
+                            "(every edge must be stored in both directions)");
             return fail(ctx, GD_EINVAL, "invalid CSR at row %d: rows must be strictly ascending, ids in [0,n), "
                         "no self-loops, and every edge stored in both directions", bad_index);
         }
@@ -800,8 +803,9 @@ static int count_batch_captured(gd_ctx *ctx, int32_t G, const std::vector<int32_
     GD_CK(ctx, cudaGraphLaunch(b->exec, st));
     GD_CK(ctx, cudaStreamSynchronize(st));
     const int32_t *h = b->h_status;
-    if (h[8]) return fail(ctx, GD_EINVAL, "invalid batch CSR: rows must be strictly ascending, ids in range, "
-                          "no self-loops, every edge stored in both directions");
+    if (h[8] || h[10] != h[11])
+        return fail(ctx, GD_EINVAL, "invalid batch CSR: rows must be strictly ascending, ids in range, "
+                    "no self-loops, every edge stored in both directions");
     if (h[1] & 1) return fail(ctx, GD_EINVAL, "an edge of the batch leaves its graph's node range");
     if (h[1]) return fail(ctx, GD_EARITH, "inconsistent batch counts (status 0x%x)", h[1]);
     return GD_OK;

@@ -34,28 +34,49 @@ using namespace gdi::dev;
 // CSR validation: sorted rows, ids in range, no self-loops, symmetric.
 // ---------------------------------------------------------------------------
 // One warp per row (hub rows have tens of thousands of entries).
-__global__ void k_validate(int32_t n, int64_t nnz, const int32_t *__restrict__ rp,
-                           const int32_t *__restrict__ ci, int32_t *status) {
+// CSR check, one warp per row: row bounds, ids in [0, n), strictly ascending
+// rows (no duplicates), no self-loops, and for every entry above the diagonal
+// (u < v) its reverse u in N(v).  status[2] / status[3] receive the numbers of
+// entries above / below the diagonal: every upper entry having its reverse
+// and the two numbers being equal makes the CSR symmetric (the reverse map of
+// the distinct upper entries is injective into the lower ones).
+__global__ void __launch_bounds__(256) k_validate(int32_t n, int64_t nnz, const int32_t *__restrict__ rp,
+                                                  const int32_t *__restrict__ ci, int32_t *status) {
     const int lane = lane_id();
+    int32_t up_all = 0, lo_all = 0;
     for (int32_t u = global_warp(); u < n; u += num_warps()) {
         const int32_t b = rp[u], e = rp[u + 1];
         // row bounds first: nothing is read through an unchecked bound
         bool bad = b < 0 || e < b || (int64_t)e > nnz;
+        int32_t up = 0, lo = 0;
         if (!bad) {
             for (int32_t p = b + lane; p < e; p += WARP) {
                 const int32_t v = ci[p];
                 bool pb = (v < 0 || v >= n || v == u || (p > b && v <= ci[p - 1]));
-                if (!pb) {
+                if (!pb && v > u) {
+                    up++;
                     const int32_t vb = rp[v], ve = rp[v + 1];
                     pb = vb < 0 || ve < vb || (int64_t)ve > nnz;
-                    // symmetric: u must appear in N(v)
                     if (!pb) pb = find_in(ci + vb, ve - vb, u) < 0;
+                } else if (!pb) {
+                    lo++;
                 }
                 bad |= pb;
             }
         }
+        up_all += up;
+        lo_all += lo;
         if (__any_sync(0xffffffffu, bad) && lane == 0) { atomicOr(status, ERR_CSR); atomicMin(status + 1, u); }
     }
+    // one pair of atomics per CTA
+    __shared__ int32_t su, sl;
+    if (threadIdx.x == 0) { su = 0; sl = 0; }
+    __syncthreads();
+    up_all = warp_sum(up_all);
+    lo_all = warp_sum(lo_all);
+    if (lane == 0) { atomicAdd(&su, up_all); atomicAdd(&sl, lo_all); }
+    __syncthreads();
+    if (threadIdx.x == 0) { atomicAdd(status + 2, su); atomicAdd(status + 3, sl); }
 }
 
 // ---------------------------------------------------------------------------
@@ -529,6 +550,10 @@ cudaError_t validate_csr(gd_graph *g, int32_t *bad_index, int32_t *bad_code) {
     if (e) return e;
     *bad_code = h[0];
     *bad_index = h[1];
+    if (!h[0] && h[2] != h[3]) {   // every upper entry has its reverse, so some lower entry has none
+        *bad_code = ERR_CSR;
+        *bad_index = -1;
+    }
     return cudaMemsetAsync(w.status, 0, 4 * sizeof(int32_t), st);
 }
 

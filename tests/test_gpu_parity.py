@@ -155,6 +155,17 @@ def test_invalid_csr_rejected(ctxs):
     del ci[int(rp[last + 1]) - 1]
     rp[last + 1:] -= 1
     cases.append((rp, np.array(ci, dtype=np.int32)))
+    # two entries below the diagonal without reverses (every entry above it
+    # keeps its reverse; only the counts above and below differ)
+    adj = [set(g.col_idx[g.row_ptr[i]:g.row_ptr[i + 1]].tolist()) for i in range(50)]
+    extra = [(x, y) for x in range(49, 0, -1) for y in range(x) if y not in adj[x]][:2]
+    assert len(extra) == 2
+    for x, y in extra:
+        adj[x].add(y)
+    rows = [sorted(a) for a in adj]
+    rp2 = np.zeros(51, dtype=np.int32)
+    rp2[1:] = np.cumsum([len(r) for r in rows])
+    cases.append((rp2, np.array([v for r in rows for v in r], dtype=np.int32)))
     for rp_, ci_ in cases:
         with pytest.raises(gd.GDError) as ei:
             ctx.graph(np.asarray(rp_, np.int32), np.asarray(ci_, np.int32), n=50, validate=True)
