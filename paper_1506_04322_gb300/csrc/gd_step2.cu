@@ -12,20 +12,21 @@
 // Triangles and 4-cliques ("bitmap" kernels).  For every node a, a team (a
 // warp for |N+(a)| <= 64, a CTA up to 1024, a CTA on global scratch above)
 // walks the pairs (c, x) with c in N+(a) and x in N+(c), the concatenated
-// out-lists spread over the lanes.  A pair whose x is in N+(a) too is the
-// triangle {a, c, x} with a lowest, found exactly once, and the scan holds
-// the CSR slots of all three of its edges:
+// out-lists spread evenly over the team's warps; a shared-memory filter and
+// hash table of N+(a) decide membership, candidates queued 32 at a time.  A
+// pair whose x is in N+(a) too is the triangle {a, c, x} with a lowest,
+// found exactly once, and the scan holds the CSR slots of all three edges:
 //   triangle {a,c,x}:  (c,x) += 1 directly, (a,c) and (a,x) through per-c
 //                      counters flushed once per node
 // The same scan sets the adjacency matrix M of the subgraph induced by
-// N+(a) (shared memory, one bit per pair).  For an edge (c, x) inside
-// N+(a), the common neighbours of c and x in M are the 4-cliques
-// {a, c, x, d} with a lowest; a second scan credits them:
+// N+(a) (shared memory, one bit per pair) and records the triangle.  For an
+// edge (c, x) inside N+(a), the common neighbours of c and x in M are the
+// 4-cliques {a, c, x, d} with a lowest; a pass over the records credits them:
 //   4-clique {a,c,x,d}: (c,x) += |M[c] & M[x]| once per inner edge,
 //                       (a,c) += half the sum over the inner edges at c
 // Per-edge |Tri_e| and cliq_e are the sums of the credits of both slots of
 // the edge.  For the global count only sum |M[c] & M[x]| = 3 K4 is kept.
-// The triangle-sum pass needs no matrix: one scan credits each triangle's
+// The triangle-sum pass walks the kept records and credits each triangle's
 // perimeter and degree sum to its three edges.
 //
 // 4-cycles.  Every 4-cycle is counted once from its highest-ranked node u
@@ -33,12 +34,16 @@
 // (wedges u-v-y with v, y below u).  Then
 //   global:   4-cycles with top u = sum_y C(cnt[y], 2)
 //   per edge: each wedge carries cnt[y]-1 cycles, credited to (u,v), (v,y).
-// Wedges are walked with a load-balanced warp loop (a warp takes 32
-// neighbours v of u and spreads their lists over its lanes).  Tables:
-//   small  : shared-memory hash per CTA (W(u) <= half its capacity)
-//   medium : dense global table per CTA (1024 threads per vertex)
-//   hubs   : a batch of hubs at a time, every CTA of the GPU working on the
-//            same few dense tables (so they stay in L2), one launch per phase.
+// A vertex's wedges are split evenly over the warps working on it (a prefix
+// of the wedge counts over N(u)); a warp walks its range 32 neighbours at a
+// time, their lists spread over the lanes.  Tables by W(u):
+//   tiny   : warp-private shared-memory hash (W <= 256)
+//   small  : shared-memory hash per CTA (W <= half its capacity)
+//   medium : one CTA per vertex, open-addressing table in global memory
+//            sized to the vertex (the tables of all CTAs fit L2 together)
+//   hubs   : W > max(2^k, n/8): a batch of hubs at a time, every warp of the
+//            GPU taking an equal share of the batch's wedges, dense tables of
+//            n counters (a few at a time, so they stay in L2).
 #include <cuda_runtime.h>
 #include <algorithm>
 #include <stdint.h>
@@ -1296,10 +1301,6 @@ __global__ void k_cycles_hub_clear(CycleArgs a) {
         c4 = warp_sum(c4);
         if (lane_id() == 0) add_u128(a.sums + 2 * (S_NUM + X_C4), 4 * c4);
     }
-}
-
-__global__ void k_zero_i32(int32_t *p, int32_t k) {
-    for (int32_t i = threadIdx.x; i < k; i += blockDim.x) p[i] = 0;
 }
 
 inline unsigned grid_for(int64_t items, int per_block, int max_blocks) {
