@@ -26,8 +26,8 @@ def ctxs():
     # a context whose shared-memory wedge table is tiny, so the global-table
     # tier of the 4-cycle kernel runs on small graphs too
     out["tiny_table"] = gd.Context(0, variant=gd.GD_VARIANT_ORIENTED, smem_table_max=256)
-    # every scheduling tier on small graphs: hub batches from 2^6 wedges, and
-    # the pairwise 4-clique path for out-degrees above 8
+    # every scheduling tier on small graphs: hub batches from max(2^6, n/8) wedges, and
+    # the global-scratch 4-clique kernel for out-degrees above 8
     out["all_tiers"] = gd.Context(0, variant=gd.GD_VARIANT_ORIENTED, smem_table_max=256,
                                   bitmap_max_outdeg=8, hub_wedges_log2=6)
     yield out
