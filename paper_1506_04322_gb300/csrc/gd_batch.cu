@@ -34,13 +34,13 @@ constexpr int NB = 14;
 enum { BERR_EDGE = 1, BERR_ARITH = 2, BERR_WIDTH = 4 };
 
 template <int NMAX, int THREADS>
-__global__ void __launch_bounds__(THREADS)
+__global__ void __launch_bounds__(THREADS, 1024 / THREADS)
 k_batch_bitmatrix(int32_t num_graphs, const int32_t *__restrict__ gnp, const int32_t *__restrict__ rp,
                   const int32_t *__restrict__ ci, int32_t *work, unsigned long long *out, int32_t *gstatus,
                   int32_t *big_list, int32_t *big_count) {
     constexpr int W = NMAX / 32;
     constexpr int NW = THREADS / 32;
-    extern __shared__ __align__(16) uint32_t M[];          // [NMAX][W]
+    extern __shared__ __align__(16) uint32_t M[];          // [NMAX][W + 1]: rows at an odd stride
     __shared__ unsigned long long red[NB][NW];
     __shared__ int32_t cur, bad;
     const int lane = lane_id(), warp = threadIdx.x >> 5;
@@ -54,9 +54,12 @@ k_batch_bitmatrix(int32_t num_graphs, const int32_t *__restrict__ gnp, const int
             if (threadIdx.x == 0) big_list[atomicAdd(big_count, 1)] = gi;
         } else {
             const int Wn = (n + 31) >> 5;
+            // odd row stride: the lanes of a warp read word w of 32 consecutive
+            // rows, which then fall in 32 different banks
+            const int Sn = Wn | 1;
             const int64_t e0 = rp[n0];
             const int64_t mg = ((int64_t)rp[n0 + n] - e0) / 2;
-            for (int k = threadIdx.x; k < n * Wn; k += THREADS) M[k] = 0;
+            for (int k = threadIdx.x; k < n * Sn; k += THREADS) M[k] = 0;
             if (threadIdx.x == 0) bad = 0;
             __syncthreads();
             // rows of bits; every edge must stay inside the graph
@@ -65,7 +68,7 @@ k_batch_bitmatrix(int32_t num_graphs, const int32_t *__restrict__ gnp, const int
                 for (int32_t p = b + lane; p < e; p += WARP) {
                     const int32_t j = ci[p] - n0;
                     if (j < 0 || j >= n || j == i) { atomicOr(&bad, BERR_EDGE); continue; }
-                    atomicOr(&M[i * Wn + (j >> 5)], 1u << (j & 31));
+                    atomicOr(&M[i * Sn + (j >> 5)], 1u << (j & 31));
                 }
             }
             __syncthreads();
@@ -77,9 +80,9 @@ k_batch_bitmatrix(int32_t num_graphs, const int32_t *__restrict__ gnp, const int
                 const int64_t di = rp[n0 + i + 1] - rp[n0 + i];
                 for (int j = i + 1 + lane; j < n; j += WARP) {
                     uint32_t c = 0;
-                    for (int w = 0; w < Wn; w++) c += __popc(M[i * Wn + w] & M[j * Wn + w]);
+                    for (int w = 0; w < Wn; w++) c += __popc(M[i * Sn + w] & M[j * Sn + w]);
                     acc[13] += (unsigned long long)c * (c - 1) / 2;
-                    if (!((M[i * Wn + (j >> 5)] >> (j & 31)) & 1u)) continue;
+                    if (!((M[i * Sn + (j >> 5)] >> (j & 31)) & 1u)) continue;
                     const int64_t dj = rp[n0 + j + 1] - rp[n0 + j];
                     const int64_t T = c, Su = di - 1 - T, Sv = dj - 1 - T, I = (int64_t)n - di - dj + T;
                     acc[0] += T; acc[1] += Su + Sv; acc[2] += I;
@@ -96,13 +99,13 @@ k_batch_bitmatrix(int32_t num_graphs, const int32_t *__restrict__ gnp, const int
                     if (T >= 2) {
                         unsigned long long pairs = 0;
                         for (int w = 0; w < Wn; w++) {
-                            uint32_t cw = M[i * Wn + w] & M[j * Wn + w];
+                            uint32_t cw = M[i * Sn + w] & M[j * Sn + w];
                             while (cw) {
                                 const int bit = __ffs(cw) - 1;
                                 cw &= cw - 1;
                                 const int x = w * 32 + bit;
                                 for (int w2 = 0; w2 < Wn; w2++)
-                                    pairs += __popc(M[x * Wn + w2] & M[i * Wn + w2] & M[j * Wn + w2]);
+                                    pairs += __popc(M[x * Sn + w2] & M[i * Sn + w2] & M[j * Sn + w2]);
                             }
                         }
                         acc[12] += pairs >> 1;
@@ -175,7 +178,7 @@ __global__ void k_batch_slice(int32_t n0, int32_t n, const int32_t *__restrict__
 
 }  // namespace
 
-size_t batch_smem_bytes(int nmax) { return (size_t)nmax * (nmax / 32) * 4; }
+size_t batch_smem_bytes(int nmax) { return (size_t)nmax * (nmax / 32 + 1) * 4; }
 
 cudaError_t launch_batch_count(gd_ctx *ctx, cudaStream_t st, int32_t num_graphs, const int32_t *gnp,
                                const int32_t *rp, const int32_t *ci, int32_t *work, unsigned long long *out,
