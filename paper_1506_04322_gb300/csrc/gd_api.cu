@@ -697,7 +697,7 @@ static int count_path(gd_graph *g, bool per_edge, uint64_t *out_dev) {
     GD_CK(ctx, run_triangles_cliques(g, per_edge, cnt));
     bool cliq_credits = per_edge, qr_credits = false;
     if (per_edge) {
-        GD_CK(ctx, run_node_sums(g));
+        GD_CK(ctx, run_node_sums(g, true));
         GD_CK(ctx, run_triangle_sums(g, cnt));
         qr_credits = true;
     }

@@ -206,15 +206,22 @@ __global__ void k_triangles(int64_t m, const int32_t *__restrict__ rp, const int
 // ---------------------------------------------------------------------------
 // Node quantities: t(x) = edges inside N(x) = sum_y T(x,y)/2; S1(x) = sum d_y
 // ---------------------------------------------------------------------------
+// nd (nullable): degree of each slot's neighbour, read in order instead of
+// through row_ptr when the schedule has built it.
 __global__ void k_node(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
-                       const uint32_t *__restrict__ tslot, uint64_t *tnode, uint64_t *s1) {
+                       const int32_t *__restrict__ nd, const uint32_t *__restrict__ tslot, uint64_t *tnode,
+                       uint64_t *s1) {
     const int lane = lane_id();
     for (int32_t x = global_warp(); x < n; x += num_warps()) {
         uint64_t a = 0, b = 0;
         for (int32_t p = rp[x] + lane; p < rp[x + 1]; p += WARP) {
             a += tslot[p];
-            int32_t y = ci[p];
-            b += (uint64_t)(rp[y + 1] - rp[y]);
+            if (nd) {
+                b += (uint64_t)nd[p];
+            } else {
+                const int32_t y = ci[p];
+                b += (uint64_t)(rp[y + 1] - rp[y]);
+            }
         }
         a = warp_sum(a); b = warp_sum(b);
         if (lane == 0) { tnode[x] = a >> 1; s1[x] = b; }
@@ -322,6 +329,7 @@ __global__ void k_literal(int64_t m, const int32_t *__restrict__ rp, const int32
 //   N_II1  = |E| - (du-1) - (dv-1) - 1 - (all edges touching the egonet)
 // ---------------------------------------------------------------------------
 struct FinalArgs {
+    const int32_t *nd;        // degree of each slot's neighbour (null: from row_ptr)
     int64_t m;
     int32_t n;
     int variant;              // 1 literal, 2 oriented
@@ -339,15 +347,22 @@ struct FinalArgs {
     int32_t *status;
 };
 
-__global__ void k_final(FinalArgs a) {
+constexpr int FINAL_THREADS = 256;
+
+__global__ void __launch_bounds__(FINAL_THREADS) k_final(FinalArgs a) {
     __shared__ unsigned long long red[S_NUM + X_NUM][8];
     unsigned long long loc[S_NUM + X_NUM];
     for (int i = 0; i < S_NUM + X_NUM; i++) loc[i] = 0;
     int bad = 0;
     const int64_t nn = a.n, mm = a.m;
-    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < a.m; k += (int64_t)gridDim.x * blockDim.x) {
+    // per-edge rows go through shared memory so that a tile of blockDim
+    // consecutive edges is written with coalesced stores (a row is 120 bytes)
+    __shared__ uint64_t stage[FINAL_THREADS * 15];
+    for (int64_t k0 = blockIdx.x * (int64_t)blockDim.x; k0 < a.m; k0 += (int64_t)gridDim.x * blockDim.x) {
+      const int64_t k = k0 + threadIdx.x;
+      if (k < a.m) {
         const int32_t u = a.eu[k], v = a.ev[k], p = a.eslot[k];
-        const int64_t du = a.rp[u + 1] - a.rp[u], dv = a.rp[v + 1] - a.rp[v];
+        const int64_t du = a.rp[u + 1] - a.rp[u], dv = a.nd ? a.nd[p] : a.rp[v + 1] - a.rp[v];
         const int64_t T = a.tslot[p];
         const int64_t Su = du - 1 - T, Sv = dv - 1 - T;
         const int64_t I = nn - du - dv + T;
@@ -403,7 +418,7 @@ __global__ void k_final(FinalArgs a) {
         const int64_t ii1 = II - (cliq + ts + ti + ss + cyc + si);
         if ((Su | Sv | I | A | DT | ts | ss | ti | cyc | si | ii1 | cliq) < 0) bad = 1;
         if (a.per_edge) {
-            uint64_t *o = a.out + k * 15;
+            uint64_t *o = stage + threadIdx.x * 15;
             o[0] = T;
             o[1] = Su + Sv;
             o[2] = I;
@@ -420,6 +435,14 @@ __global__ void k_final(FinalArgs a) {
             o[13] = (uint64_t)I * (uint64_t)(I - 1) / 2 - (uint64_t)ii1;
             o[14] = 0;
         }
+      }
+      if (a.per_edge) {
+        __syncthreads();
+        const int64_t rows = min((int64_t)blockDim.x, a.m - k0);
+        uint64_t *o = a.out + k0 * 15;
+        for (int64_t i = threadIdx.x; i < rows * 15; i += blockDim.x) o[i] = stage[i];
+        __syncthreads();
+      }
     }
     if (bad) atomicOr(a.status, ERR_NEGATIVE);
     // block reduction -> u128 atomics
@@ -593,18 +616,19 @@ cudaError_t run_triangles_intersect(gd_graph *g) {
     return cudaGetLastError();
 }
 
-cudaError_t run_node_sums(gd_graph *g) {
+cudaError_t run_node_sums(gd_graph *g, bool have_nd) {
     Workspace &w = g->ws;
     const int sms = sm_count(g);
     if (g->n > 0)
-        GD_LAUNCH(g, "k_node", k_node, grid_for((int64_t)g->n * 32, 256, sms * 16), 256, 0, g->n, g->rp, g->ci, w.tslot, w.tnode, w.s1);
+        GD_LAUNCH(g, "k_node", k_node, grid_for((int64_t)g->n * 32, 256, sms * 16), 256, 0, g->n, g->rp, g->ci,
+                  have_nd ? w.nd : nullptr, w.tslot, w.tnode, w.s1);
     return cudaGetLastError();
 }
 
 cudaError_t run_per_edge_sums(gd_graph *g) {
     Workspace &w = g->ws;
     const int sms = sm_count(g);
-    cudaError_t e = run_node_sums(g);
+    cudaError_t e = run_node_sums(g, false);
     if (e) return e;
     if (g->m > 0)
         GD_LAUNCH(g, "k_tri_sums", k_tri_sums, grid_for(g->m * 32, 256, sms * 16), 256, 0, g->m, g->rp, g->ci, w.eu, w.ev, w.tslot,
@@ -642,6 +666,7 @@ cudaError_t run_final(gd_graph *g, int variant, bool per_edge, bool cliq_credits
     a.need_restricted = per_edge ? 1 : 0;
     a.cliq_credits = cliq_credits ? 1 : 0;
     a.rp = g->rp; a.eu = w.eu; a.ev = w.ev; a.eslot = w.eslot; a.mate = w.mate; a.tslot = w.tslot;
+    a.nd = variant == GD_VARIANT_LITERAL ? nullptr : w.nd;
     a.tnode = w.tnode; a.s1 = w.s1; a.au = w.au; a.dt = w.dt;
     a.qcred = (const unsigned long long *)w.qcred;
     a.qr_credits = qr_credits ? 1 : 0;

@@ -207,7 +207,7 @@ cudaError_t run_final(gd_graph *g, int variant, bool per_edge, bool cliq_credits
 cudaError_t run_schedule(gd_graph *g, int32_t *counters_host);
 cudaError_t run_triangles_cliques(gd_graph *g, bool per_edge, const int32_t *counters_host);
 cudaError_t run_triangle_sums(gd_graph *g, const int32_t *counters_host);   // Q/R credits (needs |Tri|)
-cudaError_t run_node_sums(gd_graph *g);                                      // t(x), S1(x)
+cudaError_t run_node_sums(gd_graph *g, bool have_nd);                                      // t(x), S1(x)
 size_t clique_big_bytes(int32_t dm);
 cudaError_t clique_pairs_bytes(gd_graph *g, const int32_t *counters_host, size_t *need);
 cudaError_t run_tri_bound(gd_graph *g, int64_t *total);
