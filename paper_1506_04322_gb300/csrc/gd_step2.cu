@@ -777,7 +777,8 @@ struct CycleArgs {
     int32_t *status;             // error bits
     int32_t hub0, nhub;          // hub batch
     int64_t *hoff;               // [17] row offsets of the batch's hubs in the flat neighbour list
-    int64_t *hlen;               // [flat] wedges contributed by each neighbour
+    int64_t *hlen;               // [flat] wedges contributed by each neighbour; after the
+                                 // prefix, the neighbour's row (k_hub_rows)
     int64_t *hpre;               // [flat + 1] exclusive prefix of hlen (hpre[flat] = batch wedges)
 };
 
@@ -1185,91 +1186,178 @@ __global__ void k_hub_lengths(CycleArgs a, int32_t nh) {
     }
 }
 
+// After the prefix, hlen holds each flat entry's row instead: the CSR start
+// of the neighbour's list (low word) and the hub's index in the hub list
+// (high word), so that the walks read one word per neighbour.
+__global__ void k_hub_rows(CycleArgs a, int32_t nh) {
+    const int64_t total = a.hoff[nh];
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < total; j += (int64_t)gridDim.x * blockDim.x) {
+        int32_t lo = 0, hi = nh - 1;
+        while (lo < hi) {
+            const int32_t mid = (lo + hi + 1) >> 1;
+            if (a.hoff[mid] <= j) lo = mid; else hi = mid - 1;
+        }
+        const int32_t u = a.hubs[lo];
+        const int32_t v = a.ci[a.rp[u] + (int32_t)(j - a.hoff[lo])];
+        a.hlen[j] = (int64_t)(uint32_t)a.rp[v] | ((int64_t)lo << 32);
+    }
+}
+
+constexpr int HUB_BATCH_MAX = 16;
+
+// G consecutive 32-wedge groups of one neighbour's list in hub u's walk,
+// wedge i of this lane at ci[q0 + 32 i]: count them, or credit cnt - 1 to
+// (v, y) and add it to the lane's running credit of (u, v).
+template <int PH, int G>
+__device__ __forceinline__ void hub_groups(const CycleArgs &a, int32_t q0, int32_t u, int32_t du, uint32_t *tab,
+                                           unsigned long long &acc) {
+    int32_t y[G], dy[G];
+#pragma unroll
+    for (int i = 0; i < G; i++) { y[i] = a.ci[q0 + i * WARP]; dy[i] = a.nd[q0 + i * WARP]; }
+    if (PH == 0) {
+#pragma unroll
+        for (int i = 0; i < G; i++)
+            if (precedes(dy[i], y[i], du, u)) atomicAdd(tab + y[i], 1u);
+    } else {
+        uint32_t c[G];
+#pragma unroll
+        for (int i = 0; i < G; i++) c[i] = precedes(dy[i], y[i], du, u) ? __ldcg(tab + y[i]) : 0;
+#pragma unroll
+        for (int i = 0; i < G; i++)
+            if (c[i] > 1) {
+                atomicAdd(a.yacc + q0 + i * WARP, (unsigned long long)(c[i] - 1));
+                acc += c[i] - 1;
+            }
+    }
+}
+
 // Hub tier, phase PH (0 count, 1 credit): the batch's wedges form one flat
 // space (hub rows concatenated, each neighbour contributing its list); every
 // warp of the grid takes an equal range of it, finds the first neighbour of
-// its range by binary search in the prefix, and walks the neighbours 32 at a
-// time, clipping the lists that straddle the range ends.  Hub h counts into
-// table h.
+// its range by 32-way splits of the prefix, and walks the neighbours 32 at a
+// time, clipping the lists that straddle the range ends.  A 32-wedge group
+// that lies in one neighbour's list (most of them: hub neighbours have long
+// lists) is handled uniformly, its credits to (u, v) summed per lane until
+// the walk leaves the list; a group spanning several lists maps each lane to
+// its list by a search over the lanes' offsets.  Hub h counts into table h.
+// (Keeping two or four groups' loads in flight was measured slower: the
+// count phase is bound by the table updates in L2, not by load latency.)
 template <int PH>
 __global__ void __launch_bounds__(256, 8)
 k_cycles_hub(CycleArgs a) {
     __shared__ unsigned long long item[8][WARP];
+    __shared__ int32_t hub_u[HUB_BATCH_MAX], hub_d[HUB_BATCH_MAX], hub_b[HUB_BATCH_MAX];
+    __shared__ int64_t hub_f[HUB_BATCH_MAX];
     const int lane = lane_id(), warp = threadIdx.x >> 5;
+    if (threadIdx.x < a.nhub) {
+        const int32_t u = a.hubs[a.hub0 + threadIdx.x];
+        hub_u[threadIdx.x] = u;
+        hub_b[threadIdx.x] = a.rp[u];
+        hub_d[threadIdx.x] = a.rp[u + 1] - a.rp[u];
+        hub_f[threadIdx.x] = a.hoff[a.hub0 + threadIdx.x];
+    }
     item[warp][lane] = 0;
-    __syncwarp();
-    const int64_t *hoff = a.hoff + a.hub0;          // the batch's rows in the flat list
-    const int64_t f0 = hoff[0], flat = hoff[a.nhub];
-    const int64_t wbase = a.hpre[f0], wtot = a.hpre[flat] - wbase;
+    __syncthreads();
+    const int64_t *hpre = a.hpre;
+    const int64_t f0 = a.hoff[a.hub0], flat = a.hoff[a.hub0 + a.nhub];
+    const int64_t wbase = hpre[f0], wtot = hpre[flat] - wbase;
     // every warp of the grid takes an equal share of the batch's wedges
     const int64_t gw = global_warp(), gwn = num_warps();
-    {
-        const int64_t w_lo = wbase + wtot * gw / gwn;
-        const int64_t w_hi = wbase + wtot * (gw + 1) / gwn;
-        if (w_lo >= w_hi) return;
-        // largest j in [f0, flat) with hpre[j] <= w_lo
-        int64_t lo = f0, hi = flat;
-        while (lo < hi) {
-            const int64_t mid = (lo + hi + 1) >> 1;
-            if (a.hpre[mid] <= w_lo) lo = mid; else hi = mid - 1;
+    const int64_t w_lo = wbase + wtot * gw / gwn;
+    const int64_t w_hi = wbase + wtot * (gw + 1) / gwn;
+    if (w_lo >= w_hi) return;
+    // largest j in [f0, flat) with hpre[j] <= w_lo (hpre[flat] > w_lo): each
+    // round probes 32 evenly spaced entries of [lo, hi] and keeps one gap
+    int64_t lo = f0, hi = flat - 1;
+    while (lo < hi) {
+        const int64_t step = (hi - lo + WARP - 1) / WARP;
+        const int64_t p = lo + (int64_t)(lane + 1) * step;
+        const bool le = p <= hi && hpre[p] <= w_lo;
+        const int64_t nlo = lo + (int64_t)__popc(__ballot_sync(FULL, le)) * step;
+        hi = min(hi, nlo + step - 1);
+        lo = nlo;
+    }
+    for (int64_t j0 = lo; j0 < flat && hpre[j0] < w_hi; j0 += WARP) {
+        // lane l: neighbour j0 + l, its wedges clipped to [w_lo, w_hi)
+        const int64_t j = j0 + lane;
+        int32_t len = 0, start = 0, h = 0, slot_uv = -1;
+        if (j < flat) {
+            const int64_t p0 = hpre[j], p1 = hpre[j + 1];
+            const int64_t s0 = max(p0, w_lo), e0 = min(p1, w_hi);
+            if (e0 > s0) {
+                const int64_t row = a.hlen[j];
+                h = (int32_t)(row >> 32) - a.hub0;
+                len = (int32_t)(e0 - s0);
+                start = (int32_t)row + (int32_t)(s0 - p0);
+                slot_uv = hub_b[h] + (int32_t)(j - hub_f[h]);
+            }
         }
-        for (int64_t j0 = lo; j0 < flat && a.hpre[j0] < w_hi; j0 += WARP) {
-            // lane l: neighbour j0 + l, its wedges clipped to [w_lo, w_hi)
-            const int64_t j = j0 + lane;
-            int32_t len = 0, start = 0, u = 0, du = 0, slot_uv = -1, h = 0;
-            if (j < flat) {
-                const int64_t p0 = a.hpre[j], p1 = a.hpre[j + 1];
-                const int64_t s0 = max(p0, w_lo), e0 = min(p1, w_hi);
-                if (e0 > s0) {
-                    while (h + 1 < a.nhub && hoff[h + 1] <= j) h++;
-                    u = a.hubs[a.hub0 + h];
-                    const int32_t bu = a.rp[u];
-                    du = a.rp[u + 1] - bu;
-                    slot_uv = bu + (int32_t)(j - hoff[h]);
-                    const int32_t v = a.ci[slot_uv];
-                    len = (int32_t)(e0 - s0);
-                    start = a.rp[v] + (int32_t)(s0 - p0);
+        const int32_t incl = warp_incl_scan(len);
+        const int32_t total = __shfl_sync(FULL, incl, 31);
+        const int32_t excl = incl - len;
+        const int32_t base = start - excl;     // wedge w of lane k's list: ci[base_k + w]
+        int32_t kc = 0;                        // the lane whose list holds wedge w0
+        unsigned long long acc = 0;            // this lane's credits to (u, v) of lane kc
+        bool held = false;
+        for (int32_t w0 = 0; w0 < total;) {
+            int32_t kend = __shfl_sync(FULL, incl, kc);
+            while (kend <= w0 && kc < WARP - 1) {
+                if (PH == 1 && held) {
+                    const unsigned long long s = warp_sum(acc);
+                    if (lane == 0 && s) atomicAdd(item[warp] + kc, s);
+                    acc = 0;
+                    held = false;
                 }
+                kc++;
+                kend = __shfl_sync(FULL, incl, kc);
             }
-            const int32_t incl = warp_incl_scan(len);
-            const int32_t total = __shfl_sync(FULL, incl, 31);
-            const int32_t excl = incl - len;
-            for (int32_t w0 = 0; w0 < total; w0 += WARP) {
-                const int32_t w = w0 + lane;
-                int32_t k = 0;
-#pragma unroll
-                for (int s = 16; s >= 1; s >>= 1) {
-                    const int32_t e = __shfl_sync(FULL, excl, k + s);
-                    if (e <= w) k += s;
-                }
-                const int32_t ks = __shfl_sync(FULL, start, k);
-                const int32_t ke = __shfl_sync(FULL, excl, k);
-                const int32_t ku = __shfl_sync(FULL, u, k);
-                const int32_t kdu = __shfl_sync(FULL, du, k);
-                const int32_t kh = __shfl_sync(FULL, h, k);
-                const bool live = w < total;
-                bool ok = false;
-                int32_t q = 0, y = 0;
-                if (live) {
-                    q = ks + (w - ke);
-                    y = a.ci[q];
-                    ok = precedes(a.nd[q], y, kdu, ku);
-                }
+            if (w0 + WARP <= kend) {
+                // the group lies in lane kc's list
+                const int32_t q0 = __shfl_sync(FULL, base, kc) + w0 + lane;
+                const int32_t kh = __shfl_sync(FULL, h, kc);
                 uint32_t *tab = a.tables + (int64_t)kh * a.n;
-                if (PH == 0) {
-                    if (ok) atomicAdd(tab + y, 1u);      // result unused: a reduction
-                } else {
-                    const uint32_t c = ok ? __ldcg(tab + y) : 0;
-                    if (c > 1) atomicAdd(a.yacc + q, (unsigned long long)(c - 1));
-                    item_add(item[warp], k, c > 1 ? c - 1 : 0, live);
-                }
+                hub_groups<PH, 1>(a, q0, hub_u[kh], hub_d[kh], tab, acc);
+                w0 += WARP;
+                held = true;
+                continue;
             }
-            if (PH == 1) {
-                __syncwarp();
-                const unsigned long long s = item[warp][lane];
-                if (s) { atomicAdd(a.yacc + slot_uv, s); item[warp][lane] = 0; }
-                __syncwarp();
+            // the group spans several lists: lane -> list by search
+            const int32_t w = w0 + lane;
+            int32_t k = 0;
+#pragma unroll
+            for (int s = 16; s >= 1; s >>= 1) {
+                const int32_t e = __shfl_sync(FULL, excl, k + s);
+                if (e <= w) k += s;
             }
+            const int32_t kq = __shfl_sync(FULL, base, k);
+            const int32_t kh = __shfl_sync(FULL, h, k);
+            const bool live = w < total;
+            bool ok = false;
+            int32_t q = 0, y = 0;
+            if (live) {
+                q = kq + w;
+                y = a.ci[q];
+                ok = precedes(a.nd[q], y, hub_d[kh], hub_u[kh]);
+            }
+            uint32_t *tab = a.tables + (int64_t)kh * a.n;
+            if (PH == 0) {
+                if (ok) atomicAdd(tab + y, 1u);      // result unused: a reduction
+            } else {
+                const uint32_t c = ok ? __ldcg(tab + y) : 0;
+                if (c > 1) atomicAdd(a.yacc + q, (unsigned long long)(c - 1));
+                item_add(item[warp], k, c > 1 ? c - 1 : 0, live);
+            }
+            w0 += WARP;
+        }
+        if (PH == 1) {
+            if (held) {
+                const unsigned long long s = warp_sum(acc);
+                if (lane == 0 && s) atomicAdd(item[warp] + kc, s);
+            }
+            __syncwarp();
+            const unsigned long long s = item[warp][lane];
+            if (s) { atomicAdd(a.yacc + slot_uv, s); item[warp][lane] = 0; }
+            __syncwarp();
         }
     }
 }
@@ -1535,7 +1623,7 @@ int32_t hub_batch(gd_graph *g) {
     const int64_t per = 4 * (int64_t)(g->n > 0 ? g->n : 1);
     int64_t b = (64ll << 20) / per;
     if (b < 1) b = 1;
-    if (b > 16) b = 16;
+    if (b > HUB_BATCH_MAX) b = HUB_BATCH_MAX;
     return (int32_t)b;
 }
 
@@ -1559,12 +1647,13 @@ cudaError_t run_cycles(gd_graph *g, bool per_edge, const int32_t *cnt) {
     a.yacc = (unsigned long long *)w.yacc; a.sums = w.sums;
     a.hub0 = 0; a.nhub = 0;
     // hubs, in batches, over one flat wedge prefix of all hubs
-    const int32_t nh = cnt[C_HUB], B = hub_batch(g);
+    const int32_t nh = cnt[C_HUB], B = std::min<int32_t>(hub_batch(g), w.wtab_ctas);   // tables allocated
     a.hoff = w.hub_off; a.hlen = w.hub_len; a.hpre = w.hub_pre;
     if (nh > 0) {
         GD_LAUNCH(g, "k_hub_lengths", k_hub_lengths, grid_for(w.hub_flat, 256, sms * 8), 256, 0, a, nh);
         e = exclusive_scan_i64(g, w.hub_len, w.hub_pre, w.hub_flat, w.hub_scan_tmp);
         if (e) return e;
+        GD_LAUNCH(g, "k_hub_rows", k_hub_rows, grid_for(w.hub_flat, 256, sms * 8), 256, 0, a, nh);
     }
     for (int32_t h0 = 0; h0 < nh; h0 += B) {
         a.hub0 = h0;
