@@ -1362,8 +1362,10 @@ k_cycles_hub(CycleArgs a) {
     }
 }
 
-// Hub tier, last phase: clear the batch's tables by a full scan (a hub
-// touches a large part of its table) and sum C(cnt,2) when counting globally.
+// Hub tier, last phase: clear the batch's tables.  Counting globally, a
+// full scan reads every counter for the sum of C(cnt, 2) and zeroes the
+// nonzero ones (a hub touches a large part of its table); with per-edge
+// credits nothing is read and the tables are overwritten with zeros.
 template <bool CREDIT>
 __global__ void k_cycles_hub_clear(CycleArgs a) {
     unsigned long long c4 = 0;
@@ -1371,19 +1373,20 @@ __global__ void k_cycles_hub_clear(CycleArgs a) {
     const int64_t total4 = total >> 2;
     uint4 *t4 = reinterpret_cast<uint4 *>(a.tables);
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total4; i += (int64_t)gridDim.x * blockDim.x) {
+        if (CREDIT) {
+            t4[i] = make_uint4(0, 0, 0, 0);
+            continue;
+        }
         const uint4 v = t4[i];
         if (v.x | v.y | v.z | v.w) {
-            if (!CREDIT) c4 += c2(v.x) + c2(v.y) + c2(v.z) + c2(v.w);
+            c4 += c2(v.x) + c2(v.y) + c2(v.z) + c2(v.w);
             t4[i] = make_uint4(0, 0, 0, 0);
         }
     }
     for (int64_t i = (total4 << 2) + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
          i += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t v = a.tables[i];
-        if (v) {
-            if (!CREDIT) c4 += c2(v);
-            a.tables[i] = 0;
-        }
+        if (!CREDIT) c4 += c2(a.tables[i]);
+        a.tables[i] = 0;
     }
     if (!CREDIT) {
         c4 = warp_sum(c4);
