@@ -265,6 +265,19 @@ __device__ __forceinline__ uint32_t clique_hash(int32_t x, int bits) {
 
 constexpr int CQ = 64;   // candidate queue entries per warp
 
+// x added to a 64-bit counter in shared memory through 32-bit atomics on its
+// words (little-endian: low word first): the low word's atomic reports its
+// own wrap, which is carried into the high word, so the final value is the
+// exact sum.  Hot counters take many concurrent adds, and 32-bit shared
+// atomics serialise far less than 64-bit ones under contention.
+__device__ __forceinline__ void smem_add_u64(unsigned long long *p, unsigned long long x) {
+    uint32_t *w = reinterpret_cast<uint32_t *>(p);
+    const uint32_t lo = (uint32_t)x, hi = (uint32_t)(x >> 32);
+    const uint32_t old = atomicAdd(w, lo);
+    const uint32_t up = hi + (old + lo < old ? 1u : 0u);
+    if (up) atomicAdd(w + 1, up);
+}
+
 // Work arrays of one team (a warp or a CTA working on one node a), for an
 // out-list of at most D entries (D a multiple of 32).  Position k is the
 // k-th entry of N+(a) (ascending ids).
@@ -534,10 +547,10 @@ k_clique_bitmap(CliqueArgs a) {
                 const unsigned long long R = da + (unsigned long long)S.adeg[kc] + (unsigned long long)S.adeg[kx];
                 atomicAdd(a.qcred + 2 * (int64_t)s, P);
                 atomicAdd(a.qcred + 2 * (int64_t)s + 1, R);
-                atomicAdd(&S.qa[kc], P);
-                atomicAdd(&S.qa[kx], P);
-                atomicAdd(&S.ra[kc], R);
-                atomicAdd(&S.ra[kx], R);
+                smem_add_u64(&S.qa[kc], P);
+                smem_add_u64(&S.qa[kx], P);
+                smem_add_u64(&S.ra[kc], R);
+                smem_add_u64(&S.ra[kx], R);
             };
             if (scan) {
                 scan_pairs<TW>(a, S, D, bits, fbits, tw, [&](int32_t kc, int32_t kx, int32_t q) {
