@@ -357,10 +357,11 @@ __device__ __forceinline__ int32_t clique_find(const CliqueView &S, int32_t x, i
 // entry by walking forward from the list of the previous group's last entry
 // (no walk when the group lies inside one list).  Entries that pass the
 // filter go to the warp's queue; 32 at a time, the lanes look them up in the
-// table and call f(kc, kx, q) for every pair whose x is in N+(a) too: kc, kx
-// are the positions of c and x in N+(a), q the DAG entry of x in N+(c), so
-// dag_slot[q] is the CSR slot of (c, x).  Each such pair is the triangle
-// {a, c, x} with a lowest, found exactly once.
+// table and call f(kc, kx, q, hm) for every pair whose x is in N+(a) too: kc,
+// kx are the positions of c and x in N+(a), q the DAG entry of x in N+(c), so
+// dag_slot[q] is the CSR slot of (c, x), and hm the mask of the lanes making
+// the call together.  Each such pair is the triangle {a, c, x} with a lowest,
+// found exactly once.
 template <int TW, typename F>
 __device__ __forceinline__ void scan_pairs(const CliqueArgs &a, const CliqueView &S, int32_t D, int bits, int fbits,
                                            int tw, F f) {
@@ -370,10 +371,9 @@ __device__ __forceinline__ void scan_pairs(const CliqueArgs &a, const CliqueView
     uint16_t *qk = S.qk + tw * CQ;
     auto drain = [&](int32_t cnt) {
         __syncwarp();
-        if (lane < cnt) {
-            const int32_t kx = clique_find(S, qx[lane], bits);
-            if (kx >= 0) f((int32_t)qk[lane], kx, qq[lane]);
-        }
+        const int32_t kx = lane < cnt ? clique_find(S, qx[lane], bits) : -1;
+        const unsigned hm = __ballot_sync(FULL, kx >= 0);
+        if (kx >= 0) f((int32_t)qk[lane], kx, qq[lane], hm);
         __syncwarp();
     };
     const int32_t total = S.pre[D];
@@ -553,7 +553,7 @@ k_clique_bitmap(CliqueArgs a) {
                 smem_add_u64(&S.ra[kx], R);
             };
             if (scan) {
-                scan_pairs<TW>(a, S, D, bits, fbits, tw, [&](int32_t kc, int32_t kx, int32_t q) {
+                scan_pairs<TW>(a, S, D, bits, fbits, tw, [&](int32_t kc, int32_t kx, int32_t q, unsigned) {
                     const int32_t s = ldg(a.dag_slot + q);
                     tri_t(kc, kx, s, __ldg(a.tslot + s));
                 });
@@ -595,14 +595,21 @@ k_clique_bitmap(CliqueArgs a) {
                 if (o1 <= a.rec_cap) { rec = a.recs + o0; rcap = o1 - o0; stored = true; }
             }
             // adjacency inside N+(a), the triangle credits, the triangle record
-            scan_pairs<TW>(a, S, D, bits, fbits, tw, [&](int32_t kc, int32_t kx, int32_t q) {
+            // (the calling lanes hm often share c: one counter update per
+            // distinct position, one record-index reservation per call)
+            const unsigned lt = (1u << lane) - 1u;
+            scan_pairs<TW>(a, S, D, bits, fbits, tw, [&](int32_t kc, int32_t kx, int32_t q, unsigned hm) {
                 const int32_t s = ldg(a.dag_slot + q);
                 atomicOr(&S.M[kc * Wd + (kx >> 5)], 1u << (kx & 31));
                 atomicOr(&S.M[kx * Wd + (kc >> 5)], 1u << (kc & 31));
                 atomicAdd(a.tcred + s, 1u);
-                atomicAdd(&S.acc[kc], 1u);
+                const unsigned peers = __match_any_sync(hm, kc);
+                if ((peers & lt) == 0) atomicAdd(&S.acc[kc], (uint32_t)__popc(peers));
                 atomicAdd(&S.acc[kx], 1u);
-                const int32_t i = atomicAdd(npair, 1);
+                const int lead = __ffs(hm) - 1;
+                int32_t i = 0;
+                if (lane == lead) i = atomicAdd(npair, __popc(hm));
+                i = __shfl_sync(hm, i, lead) + __popc(hm & lt);
                 if (i < rcap)
                     rec[i] = ((unsigned long long)(uint32_t)s << 32) | ((uint32_t)kx << 16) | (uint32_t)kc;
             });
@@ -632,7 +639,7 @@ k_clique_bitmap(CliqueArgs a) {
                     inner((int32_t)(v & 0xffffu), (int32_t)((v >> 16) & 0xffffu), (int32_t)(v >> 32));
                 }
             } else if (MODE == MODE_CREDIT) {
-                scan_pairs<TW>(a, S, D, bits, fbits, tw, [&](int32_t kc, int32_t kx, int32_t q) {
+                scan_pairs<TW>(a, S, D, bits, fbits, tw, [&](int32_t kc, int32_t kx, int32_t q, unsigned) {
                     inner(kc, kx, ldg(a.dag_slot + q));
                 });
             } else {
