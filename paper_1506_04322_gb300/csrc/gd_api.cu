@@ -549,6 +549,23 @@ void gd_destroy(gd_ctx *ctx) {
 
 const char *gd_last_error(gd_ctx *ctx) { return ctx ? ctx->err.c_str() : "no context"; }
 
+// row_ptr[u] <= row_ptr[u + 1] for every row, checked a chunk at a time
+// without early exits (so the compiler vectorises the comparisons); the first
+// decreasing row goes to *bad_row.
+static bool rows_nondecreasing(const int32_t *rp, int32_t n, int32_t *bad_row) {
+    constexpr int32_t CH = 4096;
+    for (int32_t u0 = 0; u0 < n; u0 += CH) {
+        const int32_t u1 = n - u0 < CH ? n : u0 + CH;
+        int dec = 0;
+        for (int32_t u = u0; u < u1; u++) dec |= rp[u + 1] < rp[u];
+        if (dec) {
+            for (int32_t u = u0; u < u1; u++)
+                if (rp[u + 1] < rp[u]) { *bad_row = u; return false; }
+        }
+    }
+    return true;
+}
+
 int gd_create_csr(gd_ctx *ctx, int32_t n, int64_t nnz, const int32_t *row_ptr, const int32_t *col_idx,
                   int flags, void *cuda_stream, gd_graph **out) {
     if (!ctx || !out) return GD_EINVAL;
@@ -563,10 +580,9 @@ int gd_create_csr(gd_ctx *ctx, int32_t n, int64_t nnz, const int32_t *row_ptr, c
     if ((flags & GD_BORROW) && !dev) return fail(ctx, GD_EINVAL, "GD_BORROW needs GD_DEVICE_PTRS");
     GD_CK(ctx, cudaSetDevice(ctx->device));
     if (!dev) {
-        // O(n) checks of row_ptr on the host
+        // O(1) checks of row_ptr on the host; the O(n) one runs below, while
+        // the upload is in flight
         if (row_ptr[0] != 0) return fail(ctx, GD_EINVAL, "row_ptr[0] = %d, expected 0", row_ptr[0]);
-        for (int32_t u = 0; u < n; u++)
-            if (row_ptr[u + 1] < row_ptr[u]) return fail(ctx, GD_EINVAL, "row_ptr decreases at row %d", u);
         if ((int64_t)row_ptr[n] != nnz) return fail(ctx, GD_EINVAL, "row_ptr[n] = %d != nnz", row_ptr[n]);
     }
     gd_graph *g = new (std::nothrow) gd_graph();
@@ -602,6 +618,12 @@ int gd_create_csr(gd_ctx *ctx, int32_t n, int64_t nnz, const int32_t *row_ptr, c
             rc = cuda_fail(ctx, e, "CSR upload");
             gd_destroy_graph(g);
             return rc;
+        }
+        int32_t bad_row = -1;
+        if (!dev && !rows_nondecreasing(row_ptr, n, &bad_row)) {
+            cudaStreamSynchronize(g->stream);     // the upload targets blocks about to be released
+            gd_destroy_graph(g);
+            return fail(ctx, GD_EINVAL, "row_ptr decreases at row %d", bad_row);
         }
     }
     if ((rc = dalloc_n(g, &g->ws.status, 4))) { gd_destroy_graph(g); return rc; }

@@ -33,40 +33,55 @@ using namespace gdi::dev;
 // ---------------------------------------------------------------------------
 // CSR validation: sorted rows, ids in range, no self-loops, symmetric.
 // ---------------------------------------------------------------------------
-// One warp per row (hub rows have tens of thousands of entries).
-// CSR check, one warp per row: row bounds, ids in [0, n), strictly ascending
-// rows (no duplicates), no self-loops, and for every entry above the diagonal
-// (u < v) its reverse u in N(v).  status[2] / status[3] receive the numbers of
-// entries above / below the diagonal: every upper entry having its reverse
-// and the two numbers being equal makes the CSR symmetric (the reverse map of
-// the distinct upper entries is injective into the lower ones).
+// CSR check: row bounds (a thread per row), then the entries, every warp
+// taking an equal range of them (hub rows of tens of thousands of entries
+// would otherwise hold one warp for milliseconds): ids in [0, n), strictly
+// ascending rows (no duplicates), no self-loops, and for every entry above
+// the diagonal (u < v) its reverse u in N(v).  A warp finds the row of its
+// first entry by binary search over row_ptr and walks forward; every index
+// stays in bounds even when row_ptr is invalid (the row pass reports that).
+// status[2] / status[3] receive the numbers of entries above / below the
+// diagonal: every upper entry having its reverse and the two numbers being
+// equal makes the CSR symmetric (the reverse map of the distinct upper
+// entries is injective into the lower ones).
 __global__ void __launch_bounds__(256) k_validate(int32_t n, int64_t nnz, const int32_t *__restrict__ rp,
                                                   const int32_t *__restrict__ ci, int32_t *status) {
     const int lane = lane_id();
     int32_t up_all = 0, lo_all = 0;
-    for (int32_t u = global_warp(); u < n; u += num_warps()) {
+    for (int32_t u = blockIdx.x * blockDim.x + threadIdx.x; u < n; u += gridDim.x * blockDim.x) {
         const int32_t b = rp[u], e = rp[u + 1];
-        // row bounds first: nothing is read through an unchecked bound
-        bool bad = b < 0 || e < b || (int64_t)e > nnz;
-        int32_t up = 0, lo = 0;
-        if (!bad) {
-            for (int32_t p = b + lane; p < e; p += WARP) {
-                const int32_t v = ci[p];
-                bool pb = (v < 0 || v >= n || v == u || (p > b && v <= ci[p - 1]));
-                if (!pb && v > u) {
-                    up++;
-                    const int32_t vb = rp[v], ve = rp[v + 1];
-                    pb = vb < 0 || ve < vb || (int64_t)ve > nnz;
-                    if (!pb) pb = find_in(ci + vb, ve - vb, u) < 0;
-                } else if (!pb) {
-                    lo++;
-                }
-                bad |= pb;
-            }
+        if (b < 0 || e < b || (int64_t)e > nnz) { atomicOr(status, ERR_CSR); atomicMin(status + 1, u); }
+    }
+    const int64_t W = num_warps(), w = global_warp();
+    const int64_t p0 = nnz * w / W, p1 = nnz * (w + 1) / W;
+    if (n > 0 && p0 < p1) {
+        // the last row r with rp[r] <= p0
+        int32_t r = 0, hi = n - 1;
+        while (r < hi) {
+            const int32_t mid = (r + hi + 1) >> 1;
+            if ((int64_t)rp[mid] <= p0) r = mid; else hi = mid - 1;
         }
-        up_all += up;
-        lo_all += lo;
-        if (__any_sync(0xffffffffu, bad) && lane == 0) { atomicOr(status, ERR_CSR); atomicMin(status + 1, u); }
+        for (int64_t q0 = p0; q0 < p1; q0 += WARP) {
+            const int64_t p = q0 + lane;
+            int32_t u = r;
+            bool bad = false;
+            if (p < p1) {
+                while (u < n - 1 && (int64_t)rp[u + 1] <= p) u++;
+                const int32_t v = ci[p];
+                const int64_t b = rp[u];
+                bad = v < 0 || v >= n || v == u || (p > 0 && p > b && v <= ci[p - 1]);
+                if (!bad && v > u) {
+                    up_all++;
+                    const int32_t vb = rp[v], ve = rp[v + 1];
+                    bad = vb < 0 || ve < vb || (int64_t)ve > nnz;
+                    if (!bad) bad = find_in(ci + vb, ve - vb, u) < 0;
+                } else if (!bad) {
+                    lo_all++;
+                }
+            }
+            if (bad) { atomicOr(status, ERR_CSR); atomicMin(status + 1, u); }
+            r = __reduce_max_sync(0xffffffffu, (unsigned)u);
+        }
     }
     // one pair of atomics per CTA
     __shared__ int32_t su, sl;
@@ -555,7 +570,7 @@ cudaError_t max_degree(gd_graph *g, int32_t *out_host) {
 }
 
 cudaError_t launch_validate(gd_graph *g, int32_t *status) {
-    if (g->n > 0) GD_LAUNCH(g, "k_validate", k_validate, grid_for((int64_t)g->n * 32, 256, sm_count(g) * 16), 256, 0, g->n, g->nnz, g->rp, g->ci, status);
+    if (g->n > 0) GD_LAUNCH(g, "k_validate", k_validate, (unsigned)(sm_count(g) * 8), 256, 0, g->n, g->nnz, g->rp, g->ci, status);
     return cudaGetLastError();
 }
 
@@ -565,7 +580,7 @@ cudaError_t validate_csr(gd_graph *g, int32_t *bad_index, int32_t *bad_code) {
     int32_t init[4] = {0, 0x7fffffff, 0, 0};
     cudaError_t e = cudaMemcpyAsync(w.status, init, sizeof(init), cudaMemcpyHostToDevice, st);
     if (e) return e;
-    if (g->n > 0) GD_LAUNCH(g, "k_validate", k_validate, grid_for((int64_t)g->n * 32, 256, sm_count(g) * 16), 256, 0, g->n, g->nnz, g->rp, g->ci, w.status);
+    if (g->n > 0) GD_LAUNCH(g, "k_validate", k_validate, (unsigned)(sm_count(g) * 8), 256, 0, g->n, g->nnz, g->rp, g->ci, w.status);
     int32_t h[4];
     e = cudaMemcpyAsync(h, w.status, sizeof(h), cudaMemcpyDeviceToHost, st);
     if (e) return e;

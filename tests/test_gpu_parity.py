@@ -173,6 +173,20 @@ def test_invalid_csr_rejected(ctxs):
     # row_ptr that does not start at 0 is refused even without validation
     with pytest.raises(gd.GDError):
         ctx.graph(g.row_ptr + 1, g.col_idx, n=50)
+    # row_ptr decreasing at one row, both ends intact: refused from host
+    # arrays (host check) and from device arrays (device check)
+    u = next(i for i in range(1, 49) if g.row_ptr[i + 1] > g.row_ptr[i])
+    bad_rp = g.row_ptr.copy()
+    bad_rp[u], bad_rp[u + 1] = bad_rp[u + 1], bad_rp[u]
+    with pytest.raises(gd.GDError) as ei:
+        ctx.graph(bad_rp, g.col_idx, n=50)
+    assert ei.value.code == gd.GD_EINVAL and f"row {u}" in str(ei.value)
+    torch = pytest.importorskip("torch")
+    with pytest.raises(gd.GDError) as ei:
+        ctx.graph(torch.from_numpy(bad_rp).cuda(), torch.from_numpy(g.col_idx).cuda(), n=50)
+    assert ei.value.code == gd.GD_EINVAL
+    with ctx.graph(g) as h:                      # the context stays usable
+        assert h.count_global() == bruteforce.global_counts(g)
 
 
 def test_budget_refusal():
