@@ -167,16 +167,34 @@ __global__ void k_narrow(const int64_t *in, int32_t *out, int64_t len) {
         out[i] = (int32_t)in[i];
 }
 
-__global__ void k_edge_list(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+__global__ void k_edge_list(int32_t n, int64_t nnz, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
                             const int32_t *__restrict__ first_up, const int32_t *__restrict__ eoff,
                             int32_t *eu, int32_t *ev, int32_t *eslot) {
+    // every warp an equal range of the slots (a warp per row would leave one
+    // warp with each hub row); slot p of row u above the diagonal is edge
+    // eoff[u] + p - first_up[u].  The row of the range's first slot comes from
+    // a binary search over row_ptr, the next ones from walking forward.
     const int lane = lane_id();
-    for (int32_t u = global_warp(); u < n; u += num_warps()) {
-        int32_t f = first_up[u], e = rp[u + 1], o = eoff[u];
-        for (int32_t i = f + lane; i < e; i += WARP) {
-            int32_t k = o + (i - f);
-            eu[k] = u; ev[k] = ci[i]; eslot[k] = i;
+    const int64_t W = num_warps(), w = global_warp();
+    const int64_t p0 = nnz * w / W, p1 = nnz * (w + 1) / W;
+    if (n == 0 || p0 >= p1) return;
+    int32_t r = 0, hi = n - 1;
+    while (r < hi) {
+        const int32_t mid = (r + hi + 1) >> 1;
+        if ((int64_t)rp[mid] <= p0) r = mid; else hi = mid - 1;
+    }
+    for (int64_t q0 = p0; q0 < p1; q0 += WARP) {
+        const int64_t p = q0 + lane;
+        int32_t u = r;
+        if (p < p1) {
+            while (u < n - 1 && (int64_t)rp[u + 1] <= p) u++;
+            const int32_t f = first_up[u];
+            if (p >= f) {
+                const int32_t k = eoff[u] + (int32_t)(p - f);
+                eu[k] = u; ev[k] = ci[p]; eslot[k] = (int32_t)p;
+            }
         }
+        r = __reduce_max_sync(0xffffffffu, (unsigned)u);
     }
 }
 
@@ -614,7 +632,7 @@ cudaError_t prepare_edges(gd_graph *g) {
     e = exclusive_scan(g, cnt, offs, n, tmp);
     if (e) return e;
     GD_LAUNCH(g, "k_narrow", k_narrow, grid_for(n + 1, 256, sms * 8), 256, 0, offs, w.eoff, n + 1);
-    GD_LAUNCH(g, "k_edge_list", k_edge_list, grid_for((int64_t)n * 32, 256, sms * 8), 256, 0, n, g->rp, g->ci, w.first_up, w.eoff,
+    GD_LAUNCH(g, "k_edge_list", k_edge_list, (unsigned)(sms * 8), 256, 0, n, g->nnz, g->rp, g->ci, w.first_up, w.eoff,
                                                                          w.eu, w.ev, w.eslot);
     if (g->m > 0)
         GD_LAUNCH(g, "k_mate", k_mate, grid_for(g->m, 256, sms * 8), 256, 0, g->m, g->rp, g->ci, w.eu, w.ev, w.eslot, w.mate);
