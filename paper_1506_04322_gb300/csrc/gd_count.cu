@@ -382,10 +382,18 @@ struct FinalArgs {
 
 constexpr int FINAL_THREADS = 256;
 
+// Every per-edge term below is at most n^2 < 2^62 (T, Su + Sv and I are
+// parts of one partition of the n nodes), but their sums are not: C(I,2)
+// alone sums to about m n^2 / 2, past 2^64 for a sparse graph of 2^28 nodes
+// and 10^6 edges.  So every partial -- per thread, per warp, per CTA -- is
+// kept in 128 bits and reaches the global words as one 128-bit addend.
 __global__ void __launch_bounds__(FINAL_THREADS) k_final(FinalArgs a) {
-    __shared__ unsigned long long red[S_NUM + X_NUM][8];
-    unsigned long long loc[S_NUM + X_NUM];
+    __shared__ u128 red[S_NUM + X_NUM][FINAL_THREADS / 32];
+    u128 loc[S_NUM + X_NUM];
     for (int i = 0; i < S_NUM + X_NUM; i++) loc[i] = 0;
+    // adds a per-edge term (non-negative for a consistent input; a negative
+    // one raises ERR_NEGATIVE below, so its value here does not matter)
+    auto acc = [&](int i, int64_t x) { loc[i] += (u128)(uint64_t)x; };
     int bad = 0;
     const int64_t nn = a.n, mm = a.m;
     // per-edge rows go through shared memory so that a tile of blockDim
@@ -400,28 +408,28 @@ __global__ void __launch_bounds__(FINAL_THREADS) k_final(FinalArgs a) {
         const int64_t Su = du - 1 - T, Sv = dv - 1 - T;
         const int64_t I = nn - du - dv + T;
         const int64_t II = mm - du - dv + 1;      // |E| - (du-1) - (dv-1) - 1
-        loc[S_T] += T; loc[S_S] += Su + Sv; loc[S_I] += I;
-        loc[S_TT] += T * (T - 1) / 2;
-        loc[S_SUSV] += Su * Sv;
-        loc[S_TS] += T * (Su + Sv);
-        loc[S_SS] += Su * (Su - 1) / 2 + Sv * (Sv - 1) / 2;
-        loc[S_TI] += T * I;
-        loc[S_SI] += (Su + Sv) * I;
-        loc[S_II] += (uint64_t)I * (uint64_t)(I - 1) / 2;
-        loc[S_II1] += II;
-        loc[X_T2 + S_NUM] += T * T;
+        acc(S_T, T); acc(S_S, Su + Sv); acc(S_I, I);
+        acc(S_TT, T * (T - 1) / 2);
+        acc(S_SUSV, Su * Sv);
+        acc(S_TS, T * (Su + Sv));
+        acc(S_SS, Su * (Su - 1) / 2 + Sv * (Sv - 1) / 2);
+        acc(S_TI, T * I);
+        acc(S_SI, (Su + Sv) * I);
+        acc(S_II, (int64_t)((uint64_t)I * (uint64_t)(I - 1) / 2));
+        acc(S_II1, II);
+        acc(X_T2 + S_NUM, T * T);
         int64_t cliq = 0, cyc = 0, c4 = 0;
         if (a.variant == GD_VARIANT_LITERAL) {
             cliq = (int64_t)a.cacc[p];
             cyc = (int64_t)a.yacc[p];
-            loc[S_CLIQ] += cliq;
+            acc(S_CLIQ, cliq);
         } else if (a.cliq_credits) {
             const int32_t q = a.mate[p];
             cliq = (int64_t)(a.cacc[p] + a.cacc[q]);
-            loc[S_CLIQ] += cliq;
+            acc(S_CLIQ, cliq);
         }
         if (!a.need_restricted) {
-            loc[S_CYC] += cyc;
+            acc(S_CYC, cyc);
             continue;
         }
         if (a.variant != GD_VARIANT_LITERAL) {
@@ -444,7 +452,7 @@ __global__ void __launch_bounds__(FINAL_THREADS) k_final(FinalArgs a) {
         }
         const int64_t ts = A - 2 * T - 4 * cliq;
         if (a.variant != GD_VARIANT_LITERAL) cyc = c4 - ts - 2 * cliq;
-        loc[S_CYC] += cyc;
+        acc(S_CYC, cyc);
         const int64_t ss = (int64_t)a.tnode[u] + (int64_t)a.tnode[v] - 2 * T - 2 * cliq - ts;
         const int64_t ti = DT - 2 * T - 2 * cliq - ts;
         const int64_t si = ((int64_t)a.s1[u] + (int64_t)a.s1[v] - du - dv - 2 * DT - Su - Sv) - ts - 2 * ss - 2 * cyc;
@@ -478,24 +486,23 @@ __global__ void __launch_bounds__(FINAL_THREADS) k_final(FinalArgs a) {
       }
     }
     if (bad) atomicOr(a.status, ERR_NEGATIVE);
-    // block reduction -> u128 atomics
+    // block reduction in 128 bits -> one 128-bit addend per sum and CTA
     const int lane = lane_id(), warp = threadIdx.x >> 5;
     for (int i = 0; i < S_NUM + X_NUM; i++) {
-        unsigned long long x = warp_sum(loc[i]);
+        const u128 x = warp_sum_u128(loc[i]);
         if (lane == 0) red[i][warp] = x;
     }
     __syncthreads();
     if (threadIdx.x < S_NUM + X_NUM) {
-        unsigned long long s = 0;
+        u128 s = 0;
         for (int w = 0; w < (int)(blockDim.x >> 5); w++) s += red[threadIdx.x][w];
-        add_u128(a.sums + 2 * threadIdx.x, s);
+        add_u128_wide(a.sums + 2 * threadIdx.x, s);
     }
 }
 
 // ---------------------------------------------------------------------------
 // Step 4: completion (one thread), exact u128.
 // ---------------------------------------------------------------------------
-typedef unsigned __int128 u128;
 
 __device__ __forceinline__ u128 ld128(const unsigned long long *p) {
     return (u128)p[0] | ((u128)p[1] << 64);

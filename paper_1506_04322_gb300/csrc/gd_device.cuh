@@ -56,6 +56,29 @@ __device__ __forceinline__ void add_u128(unsigned long long *lohi, unsigned long
     if (old + x < old) atomicAdd(lohi + 1, 1ull);
 }
 
+typedef unsigned __int128 u128;
+
+// a full 128-bit addend into (lo, hi) words: the carry out of the low word
+// joins the high addend (concurrent adders: the total is exact mod 2^128)
+__device__ __forceinline__ void add_u128_wide(unsigned long long *lohi, u128 x) {
+    const unsigned long long lo = (unsigned long long)x;
+    unsigned long long hi = (unsigned long long)(x >> 64);
+    if (lo) {
+        const unsigned long long old = atomicAdd(lohi, lo);
+        if (old + lo < old) hi += 1;
+    }
+    if (hi) atomicAdd(lohi + 1, hi);
+}
+
+__device__ __forceinline__ u128 warp_sum_u128(u128 x) {
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long lo = __shfl_xor_sync(0xffffffffu, (unsigned long long)x, o);
+        const unsigned long long hi = __shfl_xor_sync(0xffffffffu, (unsigned long long)(x >> 64), o);
+        x += ((u128)hi << 64) | lo;
+    }
+    return x;
+}
+
 __device__ __forceinline__ int global_warp() { return (blockIdx.x * blockDim.x + threadIdx.x) >> 5; }
 __device__ __forceinline__ int num_warps() { return (gridDim.x * blockDim.x) >> 5; }
 __device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
