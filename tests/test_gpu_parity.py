@@ -240,17 +240,46 @@ def test_chung_lu_workload_global_and_per_edge(ctxs, chung_lu):
     deg = g.degrees()
     idx = rng.choice(len(e), 40, replace=False)
     small = np.flatnonzero((deg[e[:, 0]] < 200) & (deg[e[:, 1]] < 200))
-    idx = np.concatenate([idx, rng.choice(small, 60, replace=False)])
+    idx = np.concatenate([idx, rng.choice(small, 60, replace=False), hub_edges(g, e, pe, rng)])
     assert np.array_equal(pe[idx], oracle.edges_direct(g, e[idx]))
 
 
-def test_rmat_workload_global(ctxs):
+def hub_edges(g, e, pe, rng, each=20, hubs=8):
+    """Edges where the hub tiers do their work: the largest d_u + d_v, the
+    largest |Tri_e| (column g31), and edges at the highest-degree nodes."""
+    deg = g.degrees()
+    dsum = deg[e[:, 0]] + deg[e[:, 1]]
+    by_deg = np.argsort(-dsum, kind="stable")[:each]
+    by_tri = np.argsort(-pe[:, 0].astype(np.int64), kind="stable")[:each]
+    top = np.argsort(-deg, kind="stable")[:hubs]
+    at_hub = np.flatnonzero(np.isin(e[:, 0], top) | np.isin(e[:, 1], top))
+    return np.unique(np.concatenate([by_deg, by_tri, rng.choice(at_hub, each, replace=False)]))
+
+
+def test_rmat_workload_global_and_per_edge(ctxs):
+    """R-MAT scale 22 (64M edges, hubs of degree 1.6e5): global counts
+    against the O2 oracle (stored), the full per-edge matrix against them
+    through the subset-count invariant, and sampled edges -- hub edges
+    included -- against the O1 per-edge record."""
     rec = _golden("rmat_22")
     g = inputs.rmat_22()
     assert _csr_sha(g) == rec["csr_sha256"], "generator produced a different graph"
     with ctxs[gd.GD_VARIANT_ORIENTED].graph(g) as h:
         glob = h.count_global()
-    assert glob == [int(x) for x in rec["global"]]
+        pe, glob2 = h.count_per_edge()
+    want = [int(x) for x in rec["global"]]
+    assert glob == want and glob2 == want
+    edges_of = [3, 2, 1, 0, 6, 5, 4, 4, 3, 3, 3, 2, 2, 1, 0]
+    for c in range(15):
+        col = pe[:, c].astype(np.uint64)
+        # exact: two 32-bit halves, each summed below 2^58
+        total = (int((col >> np.uint64(32)).sum(dtype=np.uint64)) << 32) + \
+            int((col & np.uint64(0xFFFFFFFF)).sum(dtype=np.uint64))
+        assert total == edges_of[c] * want[c], c
+    e = g.edges()
+    rng = np.random.default_rng(321)
+    idx = np.concatenate([rng.choice(len(e), 60, replace=False), hub_edges(g, e, pe, rng)])
+    assert np.array_equal(pe[idx], oracle.edges_direct(g, e[idx]))
 
 
 def test_autotune_keeps_counts_and_caches(tmp_path):
