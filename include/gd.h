@@ -370,8 +370,11 @@ int gd_gfd_batch(gd_ctx *ctx, int32_t num_graphs, const int32_t *graph_node_ptr,
  * and stall the other streams), plug-ins whose host framework owns every
  * device byte through its own allocator, and processes under a fixed device
  * memory quota.  The scratch is one static array inside libgd's device image
- * (GD_STATIC_SCRATCH_BYTES on every GPU that loads the library, held until
- * the process exits); nothing is allocated per call.
+ * (GD_STATIC_SCRATCH_BYTES on every GPU where that image is loaded, held
+ * until the process exits); nothing is allocated per call.  The CUDA runtime
+ * loads device code lazily by default, so the first call on a device (its
+ * set-up step below) may load the image and reserve the array: make that
+ * call early, outside any latency-critical section.
  * ------------------------------------------------------------------------ */
 #define GD_STATIC_MAX_N 32768              /* largest n accepted            */
 #define GD_STATIC_MAX_NNZ 262144           /* largest nnz (= 2|E|) accepted */

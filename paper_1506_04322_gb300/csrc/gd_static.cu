@@ -8,9 +8,12 @@
 // processes under a hard device-memory quota that was planned before they
 // started.  The regular entry points (gd_create_csr + gd_count_global)
 // allocate per-graph work arrays; this one allocates nothing.  Its scratch
-// is one fixed array in the library's device image: every GPU that loads
-// libgd holds those bytes until the process exits, whether or not this entry
-// point is ever called.
+// is one fixed array in the library's device image: every GPU on which that
+// image is loaded holds those bytes until the process exits.  The CUDA
+// runtime loads device code lazily by default, so on a device where nothing
+// of this file has run yet, the first call's set-up (below) loads it, and
+// the runtime reserves the array then; make that first call early, outside
+// any latency-critical section.
 //
 // What it computes: exactly the 15 counts of gd_count_global (same order,
 // same exact u128 arithmetic), for graphs within the limits below, in ONE
@@ -141,6 +144,9 @@ k_static_global(int32_t n, int64_t nnz, const int32_t *__restrict__ rp, const in
     }
     __syncthreads();
 
+    // u64 partials are exact here: n <= MAX_N = 2^15, so every per-edge term
+    // is at most n^2 = 2^30, and a sum over the at most 2^17 edges stays
+    // below 2^47
     unsigned long long acc[NS];
     for (int i = 0; i < NS; i++) acc[i] = 0;
     const int64_t m = nnz / 2;

@@ -54,6 +54,29 @@ def test_static_entry_equals_count_global_twice_in_a_row():
                 assert _u128(out.cpu().numpy()) == want, g.name
 
 
+def test_static_entry_leaves_device_memory_unchanged():
+    """What the entry point is for: after a first call on the device (which
+    may load the library's device code and with it the static scratch), more
+    calls leave the device's free memory exactly as it was."""
+    torch = pytest.importorskip("torch")
+    g = inputs.chung_lu(20_000, 2.2, 60_000, 0.0, 3)
+    rp = torch.from_numpy(g.row_ptr).cuda()
+    ci = torch.from_numpy(g.col_idx).cuda()
+    out = torch.empty(30, dtype=torch.int64, device="cuda")
+    stream = torch.cuda.current_stream().cuda_stream
+    assert gd.gd_count_global_static(g.n, g.nnz, rp.data_ptr(), ci.data_ptr(), out.data_ptr(), stream) == gd.GD_OK
+    torch.cuda.synchronize()
+    want = _u128(out.cpu().numpy())
+    free_before, _ = torch.cuda.mem_get_info()
+    for _ in range(5):
+        rc = gd.gd_count_global_static(g.n, g.nnz, rp.data_ptr(), ci.data_ptr(), out.data_ptr(), stream)
+        assert rc == gd.GD_OK
+    torch.cuda.synchronize()
+    free_after, _ = torch.cuda.mem_get_info()
+    assert free_after == free_before
+    assert _u128(out.cpu().numpy()) == want
+
+
 def test_static_entry_rejects_sizes_beyond_its_scratch():
     torch = pytest.importorskip("torch")
     rp = torch.zeros(4, dtype=torch.int32, device="cuda")
