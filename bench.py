@@ -55,6 +55,7 @@ def parse():
     ap.add_argument("--smem-table", type=int, default=None, help="gd_options.smem_table_max")
     ap.add_argument("--bitmap-max", type=int, default=None, help="gd_options.bitmap_max_outdeg")
     ap.add_argument("--hub-log2", type=int, default=None, help="gd_options.hub_wedges_log2")
+    ap.add_argument("--hub-pull", type=int, default=None, help="gd_options.hub_pull (0 auto, 1 never, 2 always)")
     ap.add_argument("--global-only", action="store_true", help="time gd_count_global instead")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-graphs measurement")
     ap.add_argument("--no-serving", action="store_true", help="skip the request-loop measurement")
@@ -502,7 +503,7 @@ def run_gd(args):
     m = g.m
 
     ctx = gd.Context(device, smem_table_max=args.smem_table, bitmap_max_outdeg=args.bitmap_max,
-                     hub_wedges_log2=args.hub_log2)
+                     hub_wedges_log2=args.hub_log2, hub_pull=args.hub_pull)
     stream = torch.cuda.Stream(device=device)
     rp = torch.from_numpy(g.row_ptr).to(device)
     ci = torch.from_numpy(g.col_idx).to(device)

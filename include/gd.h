@@ -119,8 +119,16 @@ typedef struct gd_options {
                                  processed by the whole GPU in batches (dense
                                  tables of n counters); below, one CTA per vertex
                                  with a table sized to its wedges (default 17) */
-    int32_t reserved[6];
+    int32_t hub_pull;         /* global counts only: GD_PULL_AUTO (default) counts
+                                 the heaviest hubs, 64 at a time, by summing per-node
+                                 hub bit masks at each opposite node while a batch
+                                 has at least nnz/2 wedges, the rest by counter
+                                 updates; GD_PULL_NEVER, GD_PULL_ALWAYS force one
+                                 form for every hub (the counts are the same)      */
+    int32_t reserved[5];
 } gd_options;
+
+enum { GD_PULL_AUTO = 0, GD_PULL_NEVER = 1, GD_PULL_ALWAYS = 2 };
 
 /* Fill *opt with the defaults. */
 void gd_default_options(gd_options *opt);

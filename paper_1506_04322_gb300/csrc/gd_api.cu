@@ -256,6 +256,12 @@ size_t estimate_footprint(gd_ctx *ctx, int64_t n, int64_t nnz, bool per_edge, bo
         b += round_block((size_t)std::min<int64_t>(8 * cap * ctas, std::max<int64_t>(8 * cap, medium_table_limit(nnz))));
     }
     if (per_edge) b += round_block(sizeof(unsigned long long) * 2 * (size_t)nnz);   // triangle records (typical)
+    if (!per_edge && n > 0) {
+        // pull form of the hub tier: node masks, chunks, heavy-node counters
+        const size_t items = (size_t)(nnz / 64 + nnz / 1024 + 1), heavy = (size_t)(nnz / 1024 + 1);
+        b += round_block(8 * (size_t)n) + round_block(12 * items) + round_block(4 * heavy) +
+             round_block(256 * heavy) + round_block(8);
+    }
     g.ws = Workspace();
     return b;
 }
@@ -345,10 +351,25 @@ int ensure_medium_scratch(gd_graph *g, const int32_t *cnt) {
 
 // Flat neighbour lists of the hubs: row offsets (from the hub list), then
 // lengths, prefix and scan scratch sized to the hubs' concatenated rows.
-int ensure_hub_scratch(gd_graph *g, const int32_t *cnt) {
+int ensure_hub_scratch(gd_graph *g, const int32_t *cnt, bool per_edge) {
     Workspace &w = g->ws;
     const int32_t nh = cnt[C_HUB];
     int rc;
+    if (!per_edge && !w.pull_mask) {
+        // hub masks of the pull form (global counts); zero at rest, cleared
+        // here once and by every pull batch after use
+        // a node of degree >= 64 takes at least 64 slots: at most nnz / 64 of
+        // them, with at most nnz / 1024 further chunks; a node of several
+        // chunks has degree > 1024
+        const int64_t items = g->nnz / 64 + g->nnz / 1024 + 1, heavy = g->nnz / 1024 + 1;
+        if ((rc = dalloc_n(g, &w.pull_mask, (int64_t)g->n))) return rc;
+        if ((rc = dalloc_n(g, &w.pull_items, 3 * items))) return rc;
+        if ((rc = dalloc_n(g, &w.pull_heavy_y, heavy))) return rc;
+        if ((rc = dalloc_n(g, &w.pull_heavy_cnt, 64 * heavy))) return rc;
+        if ((rc = dalloc_n(g, &w.pull_counts, 2))) return rc;
+        GD_CK(g->ctx, cudaMemsetAsync(w.pull_mask, 0, sizeof(unsigned long long) * (size_t)g->n, g->stream));
+        GD_CK(g->ctx, cudaMemsetAsync(w.pull_heavy_cnt, 0, sizeof(uint32_t) * 64 * (size_t)heavy, g->stream));
+    }
     if (!w.hub_off || w.hub_off_cap < nh + 1) {
         if (w.hub_off) { release_block(g, w.hub_off); w.hub_off = nullptr; }
         if ((rc = dalloc_n(g, &w.hub_off, (int64_t)nh + 1))) return rc;
@@ -487,6 +508,7 @@ static int check_options(gd_options *o) {
     if (o->hub_wedges_log2 == 0) o->hub_wedges_log2 = 17;
     if (o->bitmap_max_outdeg < 2 || o->bitmap_max_outdeg > gdi::CL_D2 || o->hub_wedges_log2 < 4 ||
         o->hub_wedges_log2 > 40) return GD_EINVAL;
+    if (o->hub_pull < GD_PULL_AUTO || o->hub_pull > GD_PULL_ALWAYS) return GD_EINVAL;
     return GD_OK;
 }
 
@@ -708,7 +730,7 @@ static int count_path(gd_graph *g, bool per_edge, uint64_t *out_dev) {
     int32_t cnt[C_NUM];
     GD_CK(ctx, run_schedule(g, cnt));
     if (cnt[C_CL0 + 3] > 0 && (rc = ensure_clique_scratch(g, cnt))) return rc;
-    if (cnt[C_HUB] > 0 && (rc = ensure_hub_scratch(g, cnt))) return rc;
+    if (cnt[C_HUB] > 0 && (rc = ensure_hub_scratch(g, cnt, per_edge))) return rc;
     if (cnt[C_MEDIUM] > 0 && (rc = ensure_medium_scratch(g, cnt))) return rc;
     if ((rc = ensure_pairs(g, cnt))) return rc;
     if (per_edge) {

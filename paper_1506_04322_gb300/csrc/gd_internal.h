@@ -99,6 +99,11 @@ struct Workspace {
     int32_t *mlist = nullptr;      // [n] medium tier sorted by decreasing wedge work
     int64_t *hub_off = nullptr, *hub_len = nullptr, *hub_pre = nullptr, *hub_scan_tmp = nullptr;
     int64_t hub_flat_cap = 0;      // capacity of hub_len / hub_pre
+    unsigned long long *pull_mask = nullptr;   // [n] global counts: batch-hub bits per node (zero at rest)
+    int32_t *pull_items = nullptr;         // [3 * (nnz/64 + nnz/1024 + 1)] chunks of the high-degree nodes
+    int32_t *pull_heavy_y = nullptr;       // [nnz/1024 + 1] nodes of several chunks
+    uint32_t *pull_heavy_cnt = nullptr;    // [64 * (nnz/1024 + 1)] their per-hub counters (zero at rest)
+    int32_t *pull_counts = nullptr;        // [2] chunks, heavy nodes
     int64_t hub_flat = 0;          // the hubs' concatenated rows (this count call)
     int32_t hub_off_cap = 0;       // capacity of hub_off
     int32_t *tlist = nullptr;      // [n] tiny tier (warp per vertex)

@@ -45,7 +45,9 @@
 //            GPU taking an equal share of the batch's wedges, dense tables of
 //            n counters (a few at a time, so they stay in L2).
 #include <cuda_runtime.h>
+
 #include <algorithm>
+#include <vector>
 #include <stdint.h>
 
 #include "gd_device.cuh"
@@ -1382,6 +1384,231 @@ k_cycles_hub(CycleArgs a) {
     }
 }
 
+// ---------------------------------------------------------------------------
+// Hub tier, global counts, pull form (heaviest hubs).  For a batch of up to
+// 64 hubs u_i in decreasing rank, the 4-cycles with top node u_i and
+// opposite node y number C(cnt_i[y], 2), cnt_i[y] = #{v in N(y): v below
+// u_i and adjacent to it} (y below u_i).  Instead of one counter update per
+// wedge, every node v carries the bits M[v] of the batch hubs above it that
+// it is adjacent to, and each y sums the masks of its neighbours into
+// bit-plane counters: plane a holds bit a of all 64 counters, so adding a
+// mask is a ripple of ANDs and XORs.  Then
+//   sum_i C(cnt_i, 2) = (sum_{a,b} 2^(a+b) |P_a & P_b & V| - sum_a 2^a |P_a & V|) / 2
+// with V the hubs ranked above y.  No tables, no atomics: one read of
+// N(y) and its neighbours' masks per y and batch.
+// ---------------------------------------------------------------------------
+constexpr int PULL_MAX = 64;          // hubs per pull batch (bits of a mask)
+constexpr int PULL_WARP_DEG = 64;     // d_y >= this: a warp per y, else a thread
+constexpr int PULL_TPLANES = 7;       // thread path: counters <= 63
+
+// mark (set) or clear the masks of the lower neighbours of hubs [h0, h0 + nb)
+template <bool SET>
+__global__ void k_pull_mark(CycleArgs a, int32_t h0, int32_t nb, unsigned long long *mask) {
+    const int64_t f0 = a.hoff[h0], f1 = a.hoff[h0 + nb];
+    for (int64_t j = f0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < f1; j += (int64_t)gridDim.x * blockDim.x) {
+        int32_t lo = h0, hi = h0 + nb - 1;
+        while (lo < hi) {
+            const int32_t mid = (lo + hi + 1) >> 1;
+            if (a.hoff[mid] <= j) lo = mid; else hi = mid - 1;
+        }
+        const int32_t u = a.hubs[lo];
+        const int32_t bu = a.rp[u], du = a.rp[u + 1] - bu;
+        const int32_t p = bu + (int32_t)(j - a.hoff[lo]);
+        const int32_t v = a.ci[p];
+        if (!SET) mask[v] = 0;
+        else if (precedes(a.nd[p], v, du, u)) atomicOr(mask + v, 1ull << (lo - h0));
+    }
+}
+
+template <int L>
+__device__ __forceinline__ void plane_add(unsigned long long (&P)[L], unsigned long long x) {
+#pragma unroll
+    for (int b = 0; b < L; b++) {
+        const unsigned long long c = P[b] & x;
+        P[b] ^= x;
+        x = c;
+    }
+}
+
+// sum over the hubs of V of C(cnt, 2), the counters held as L bit planes
+template <int L>
+__device__ __forceinline__ unsigned long long plane_pairs(const unsigned long long (&P)[L], unsigned long long V) {
+    unsigned long long s1 = 0, s2 = 0;
+#pragma unroll
+    for (int a0 = 0; a0 < L; a0++) {
+        const unsigned long long pa = P[a0] & V;
+        s1 += (unsigned long long)__popcll(pa) << a0;
+        s2 += (unsigned long long)__popcll(pa) << (2 * a0);
+#pragma unroll
+        for (int b = 0; b < L; b++)
+            if (b > a0) s2 += (unsigned long long)__popcll(pa & P[b]) << (a0 + b + 1);
+    }
+    return (s2 - s1) >> 1;
+}
+
+// the hubs of the batch ranked above y: the first k (hubs in decreasing rank)
+__device__ __forceinline__ unsigned long long hubs_above(int32_t dy, int32_t y, const int32_t *hd,
+                                                         const int32_t *hu, int32_t nb) {
+    int32_t lo = 0, hi = nb;
+    while (lo < hi) {
+        const int32_t mid = (lo + hi) >> 1;
+        if (precedes(dy, y, hd[mid], hu[mid])) lo = mid + 1; else hi = mid;
+    }
+    return lo >= 64 ? ~0ull : ((1ull << lo) - 1);
+}
+
+__device__ __forceinline__ void pull_hubs_smem(const CycleArgs &a, int32_t h0, int32_t nb, int32_t *hu, int32_t *hd) {
+    if (threadIdx.x < nb) {
+        const int32_t u = a.hubs[h0 + threadIdx.x];
+        hu[threadIdx.x] = u;
+        hd[threadIdx.x] = a.rp[u + 1] - a.rp[u];
+    }
+    __syncthreads();
+}
+
+// A thread per node y of degree < PULL_WARP_DEG; the neighbours' masks are
+// fetched four at a time so that four loads are in flight per thread.
+__global__ void __launch_bounds__(256)
+k_pull_thread(CycleArgs a, int32_t h0, int32_t nb, const unsigned long long *__restrict__ mask) {
+    __shared__ int32_t hu[PULL_MAX], hd[PULL_MAX];
+    pull_hubs_smem(a, h0, nb, hu, hd);
+    unsigned long long c4 = 0;
+    for (int32_t y = blockIdx.x * blockDim.x + threadIdx.x; y < a.n; y += gridDim.x * blockDim.x) {
+        const int32_t b = __ldg(a.rp + y), e = __ldg(a.rp + y + 1), d = e - b;
+        if (d < 2 || d >= PULL_WARP_DEG) continue;
+        unsigned long long P[PULL_TPLANES] = {0, 0, 0, 0, 0, 0, 0};
+        int32_t p = b;
+        for (; p + 4 <= e; p += 4) {
+            const int32_t v0 = __ldg(a.ci + p), v1 = __ldg(a.ci + p + 1);
+            const int32_t v2 = __ldg(a.ci + p + 2), v3 = __ldg(a.ci + p + 3);
+            const unsigned long long m0 = mask[v0], m1 = mask[v1], m2 = mask[v2], m3 = mask[v3];
+            plane_add<PULL_TPLANES>(P, m0);
+            plane_add<PULL_TPLANES>(P, m1);
+            plane_add<PULL_TPLANES>(P, m2);
+            plane_add<PULL_TPLANES>(P, m3);
+        }
+        for (; p < e; p++) plane_add<PULL_TPLANES>(P, mask[__ldg(a.ci + p)]);
+        unsigned long long any = 0;
+#pragma unroll
+        for (int i = 1; i < PULL_TPLANES; i++) any |= P[i];
+        if (!any) continue;                   // every counter <= 1
+        c4 += plane_pairs<PULL_TPLANES>(P, hubs_above(d, y, hd, hu, nb));
+    }
+    c4 = warp_sum(c4);
+    if (lane_id() == 0 && c4) add_u128(a.sums + 2 * (S_NUM + X_C4), 4 * c4);
+}
+
+// Nodes of degree >= PULL_WARP_DEG are split into chunks of at most
+// PULL_CHUNK neighbours, one warp per chunk (the list of chunks is built
+// once per count: the degrees do not change between batches).  A node of
+// one chunk gets its C(cnt, 2) sum from the chunk's planes; a node of
+// several chunks (a "heavy" node) adds each chunk's per-hub counters into
+// 64 counters of its own, summed by k_pull_heavy after all chunks.
+constexpr int PULL_CHUNK = 1024;
+constexpr int PULL_CPLANES = 11;      // a chunk's counters are <= 1024
+
+struct PullItem { int32_t y, chunk, heavy; };
+
+__global__ void k_pull_items(int32_t n, const int32_t *__restrict__ rp, PullItem *items, int32_t *heavy_y,
+                             int32_t *counts) {
+    for (int32_t y = blockIdx.x * blockDim.x + threadIdx.x; y < n; y += gridDim.x * blockDim.x) {
+        const int32_t d = rp[y + 1] - rp[y];
+        if (d < PULL_WARP_DEG) continue;
+        const int32_t nch = (d + PULL_CHUNK - 1) / PULL_CHUNK;
+        const int32_t pos = atomicAdd(counts, nch);
+        int32_t hv = -1;
+        if (nch > 1) { hv = atomicAdd(counts + 1, 1); heavy_y[hv] = y; }
+        for (int32_t c = 0; c < nch; c++) items[pos + c] = PullItem{y, c, hv};
+    }
+}
+
+__global__ void __launch_bounds__(256)
+k_pull_warp(CycleArgs a, int32_t h0, int32_t nb, const unsigned long long *__restrict__ mask,
+            const PullItem *__restrict__ items, int32_t nitems, uint32_t *heavy_cnt) {
+    __shared__ int32_t hu[PULL_MAX], hd[PULL_MAX];
+    pull_hubs_smem(a, h0, nb, hu, hd);
+    const int lane = lane_id();
+    unsigned long long c4 = 0;
+    for (int64_t it = global_warp(); it < nitems; it += num_warps()) {
+        const PullItem t = items[it];
+        const int32_t b0 = __ldg(a.rp + t.y), d = __ldg(a.rp + t.y + 1) - b0;
+        const int32_t b = b0 + t.chunk * PULL_CHUNK, e = min(b + PULL_CHUNK, b0 + d);
+        unsigned long long P[PULL_CPLANES];
+#pragma unroll
+        for (int i = 0; i < PULL_CPLANES; i++) P[i] = 0;
+        int32_t p = b + lane;
+        for (; p + 3 * WARP < e; p += 4 * WARP) {
+            const int32_t v0 = __ldg(a.ci + p), v1 = __ldg(a.ci + p + WARP);
+            const int32_t v2 = __ldg(a.ci + p + 2 * WARP), v3 = __ldg(a.ci + p + 3 * WARP);
+            const unsigned long long m0 = mask[v0], m1 = mask[v1], m2 = mask[v2], m3 = mask[v3];
+            plane_add<PULL_CPLANES>(P, m0);
+            plane_add<PULL_CPLANES>(P, m1);
+            plane_add<PULL_CPLANES>(P, m2);
+            plane_add<PULL_CPLANES>(P, m3);
+        }
+        for (; p < e; p += WARP) plane_add<PULL_CPLANES>(P, mask[__ldg(a.ci + p)]);
+        // butterfly: every lane ends with the chunk's total (<= 1024 each)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            unsigned long long c = 0;
+#pragma unroll
+            for (int i = 0; i < PULL_CPLANES; i++) {
+                const unsigned long long q = __shfl_xor_sync(FULL, P[i], o);
+                const unsigned long long s = P[i] ^ q ^ c;
+                c = (P[i] & q) | (c & (P[i] ^ q));
+                P[i] = s;
+            }
+        }
+        if (t.heavy < 0) {
+            if (lane == 0) c4 += plane_pairs<PULL_CPLANES>(P, hubs_above(d, t.y, hd, hu, nb));
+        } else {
+            // lane l: counters of hubs l and l + 32 out of the planes
+            uint32_t x0 = 0, x1 = 0;
+#pragma unroll
+            for (int i = 0; i < PULL_CPLANES; i++) {
+                x0 |= (uint32_t)((P[i] >> lane) & 1ull) << i;
+                x1 |= (uint32_t)((P[i] >> (lane + 32)) & 1ull) << i;
+            }
+            uint32_t *hc = heavy_cnt + (int64_t)t.heavy * PULL_MAX;
+            if (x0) atomicAdd(hc + lane, x0);
+            if (x1) atomicAdd(hc + lane + 32, x1);
+        }
+    }
+    c4 = warp_sum(c4);
+    if (lane == 0 && c4) add_u128(a.sums + 2 * (S_NUM + X_C4), 4 * c4);
+}
+
+// heavy nodes: sum C(cnt, 2) over the hubs above y, and reset the counters
+__global__ void k_pull_heavy(CycleArgs a, int32_t h0, int32_t nb, const int32_t *__restrict__ heavy_y,
+                             int32_t nheavy, uint32_t *heavy_cnt) {
+    __shared__ int32_t hu[PULL_MAX], hd[PULL_MAX];
+    pull_hubs_smem(a, h0, nb, hu, hd);
+    const int lane = lane_id();
+    unsigned long long c4 = 0;
+    for (int64_t k = global_warp(); k < nheavy; k += num_warps()) {
+        const int32_t y = heavy_y[k];
+        const int32_t d = __ldg(a.rp + y + 1) - __ldg(a.rp + y);
+        const unsigned long long V = hubs_above(d, y, hd, hu, nb);
+        uint32_t *hc = heavy_cnt + k * PULL_MAX;
+        const uint32_t x0 = hc[lane], x1 = hc[lane + 32];
+        hc[lane] = 0;
+        hc[lane + 32] = 0;
+        unsigned long long t = 0;
+        if ((V >> lane) & 1ull) t += c2(x0);
+        if ((V >> (lane + 32)) & 1ull) t += c2(x1);
+        t = warp_sum(t);
+        if (lane == 0) c4 += t;
+    }
+    c4 = warp_sum(c4);
+    if (lane == 0 && c4) add_u128(a.sums + 2 * (S_NUM + X_C4), 4 * c4);
+}
+
+// per-hub wedge work at the hub boundaries of the flat prefix
+__global__ void k_hub_work(int32_t nh, const int64_t *hoff, const int64_t *hpre, int64_t *out) {
+    for (int32_t h = blockIdx.x * blockDim.x + threadIdx.x; h <= nh; h += gridDim.x * blockDim.x)
+        out[h] = hpre[hoff[h]];
+}
+
 // Hub tier, last phase: clear the batch's tables.  Counting globally, a
 // full scan reads every counter for the sum of C(cnt, 2) and zeroes the
 // nonzero ones (a hub touches a large part of its table); with per-edge
@@ -1577,7 +1804,27 @@ cudaError_t run_hub_offsets(gd_graph *g, int32_t nh, int64_t *flat) {
     if (nh == 0) return cudaSuccess;
     GD_LAUNCH(g, "k_hub_degrees", k_hub_degrees, grid_for(nh, 256, sms_of(g) * 4), 256, 0, nh, w.hubs, g->rp,
               w.scan_tmp);
-    cudaError_t e = exclusive_scan_i64(g, w.scan_tmp, w.hub_off, nh, w.scan_tmp + (nh + 1));
+    // hubs in decreasing rank (degree, then id): the heaviest come first,
+    // and a batch holds hubs of similar degree
+    std::vector<int32_t> ids(nh);
+    std::vector<int64_t> deg(nh);
+    cudaError_t e = cudaMemcpyAsync(ids.data(), w.hubs, sizeof(int32_t) * (size_t)nh, cudaMemcpyDeviceToHost, g->stream);
+    if (!e) e = cudaMemcpyAsync(deg.data(), w.scan_tmp, sizeof(int64_t) * (size_t)nh, cudaMemcpyDeviceToHost, g->stream);
+    if (!e) e = cudaStreamSynchronize(g->stream);
+    if (e) return e;
+    std::vector<int32_t> order(nh);
+    for (int32_t i = 0; i < nh; i++) order[i] = i;
+    std::sort(order.begin(), order.end(), [&](int32_t x, int32_t y) {
+        return deg[x] != deg[y] ? deg[x] > deg[y] : ids[x] > ids[y];
+    });
+    std::vector<int32_t> sorted(nh);
+    std::vector<int64_t> sdeg(nh);
+    for (int32_t i = 0; i < nh; i++) { sorted[i] = ids[order[i]]; sdeg[i] = deg[order[i]]; }
+    e = cudaMemcpyAsync(w.hubs, sorted.data(), sizeof(int32_t) * (size_t)nh, cudaMemcpyHostToDevice, g->stream);
+    if (!e) e = cudaMemcpyAsync(w.scan_tmp, sdeg.data(), sizeof(int64_t) * (size_t)nh, cudaMemcpyHostToDevice, g->stream);
+    if (!e) e = cudaStreamSynchronize(g->stream);
+    if (e) return e;
+    e = exclusive_scan_i64(g, w.scan_tmp, w.hub_off, nh, w.scan_tmp + (nh + 1));
     if (e) return e;
     e = cudaMemcpyAsync(flat, w.hub_off + nh, sizeof(int64_t), cudaMemcpyDeviceToHost, g->stream);
     if (e) return e;
@@ -1678,7 +1925,48 @@ cudaError_t run_cycles(gd_graph *g, bool per_edge, const int32_t *cnt) {
         if (e) return e;
         GD_LAUNCH(g, "k_hub_rows", k_hub_rows, grid_for(w.hub_flat, 256, sms * 8), 256, 0, a, nh);
     }
-    for (int32_t h0 = 0; h0 < nh; h0 += B) {
+    int32_t first_push = 0;
+    const int pull = g->ctx->opt.hub_pull;
+    if (!per_edge && nh > 0 && w.pull_mask && pull != GD_PULL_NEVER) {
+        // global counts: the heaviest hubs, 64 at a time, in pull form while
+        // a batch's wedges are at least half the CSR slots (a pull pass reads
+        // every slot once; a push pass updates a counter per wedge and clears
+        // its dense tables)
+        std::vector<int64_t> hw(nh + 1);
+        GD_LAUNCH(g, "k_hub_work", k_hub_work, grid_for(nh + 1, 256, sms * 4), 256, 0, nh,
+                  (const int64_t *)w.hub_off, (const int64_t *)w.hub_pre, w.scan_tmp);
+        e = cudaMemcpyAsync(hw.data(), w.scan_tmp, sizeof(int64_t) * (size_t)(nh + 1), cudaMemcpyDeviceToHost, g->stream);
+        if (!e) e = cudaStreamSynchronize(g->stream);
+        if (e) return e;
+        // the chunks of the nodes of degree >= PULL_WARP_DEG (once per count)
+        int32_t pc[2] = {0, 0};
+        PullItem *items = reinterpret_cast<PullItem *>(w.pull_items);
+        e = cudaMemsetAsync(w.pull_counts, 0, 2 * sizeof(int32_t), g->stream);
+        if (e) return e;
+        GD_LAUNCH(g, "k_pull_items", k_pull_items, grid_for(g->n, 256, sms * 8), 256, 0, g->n, g->rp, items,
+                  w.pull_heavy_y, w.pull_counts);
+        e = cudaMemcpyAsync(pc, w.pull_counts, sizeof(pc), cudaMemcpyDeviceToHost, g->stream);
+        if (!e) e = cudaStreamSynchronize(g->stream);
+        if (e) return e;
+        while (first_push < nh) {
+            const int32_t nb = std::min<int32_t>(PULL_MAX, nh - first_push);
+            if (pull == GD_PULL_AUTO && hw[first_push + nb] - hw[first_push] < g->nnz / 2) break;
+            const unsigned grid_f = grid_for(w.hub_flat, 256, sms * 8);
+            GD_LAUNCH(g, "k_pull_mark", k_pull_mark<true>, grid_f, 256, 0, a, first_push, nb, w.pull_mask);
+            GD_LAUNCH(g, "k_pull_thread", k_pull_thread, (unsigned)(sms * 8), 256, 0, a, first_push, nb,
+                      (const unsigned long long *)w.pull_mask);
+            if (pc[0] > 0)
+                GD_LAUNCH(g, "k_pull_warp", k_pull_warp, grid_for((int64_t)pc[0] * 32, 256, sms * 8), 256, 0, a,
+                          first_push, nb, (const unsigned long long *)w.pull_mask, (const PullItem *)items, pc[0],
+                          w.pull_heavy_cnt);
+            if (pc[1] > 0)
+                GD_LAUNCH(g, "k_pull_heavy", k_pull_heavy, grid_for((int64_t)pc[1] * 32, 256, sms * 8), 256, 0, a,
+                          first_push, nb, (const int32_t *)w.pull_heavy_y, pc[1], w.pull_heavy_cnt);
+            GD_LAUNCH(g, "k_pull_clear", k_pull_mark<false>, grid_f, 256, 0, a, first_push, nb, w.pull_mask);
+            first_push += nb;
+        }
+    }
+    for (int32_t h0 = first_push; h0 < nh; h0 += B) {
         a.hub0 = h0;
         a.nhub = nh - h0 < B ? nh - h0 : B;
         GD_LAUNCH(g, "k_cycles_hub_count", k_cycles_hub<0>, (unsigned)(sms * 8), 256, 0, a);

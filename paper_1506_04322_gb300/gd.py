@@ -36,6 +36,7 @@ GD_DEVICE_PTRS, GD_VALIDATE, GD_BORROW = 1, 2, 4
 GD_OUT_DEVICE = 1
 GD_CAPTURE = 8
 GD_VARIANT_AUTO, GD_VARIANT_LITERAL, GD_VARIANT_ORIENTED = 0, 1, 2
+GD_PULL_AUTO, GD_PULL_NEVER, GD_PULL_ALWAYS = 0, 1, 2
 
 
 class GDError(RuntimeError):
@@ -66,7 +67,7 @@ class gd_options(ctypes.Structure):
     _fields_ = [("variant", ctypes.c_int32), ("block_threads", ctypes.c_int32),
                 ("ctas_per_sm", ctypes.c_int32), ("smem_table_max", ctypes.c_int32),
                 ("bitmap_max_outdeg", ctypes.c_int32), ("hub_wedges_log2", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 6)]
+                ("hub_pull", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
 
 
 class gd_tune_result(ctypes.Structure):
@@ -377,9 +378,11 @@ class Context:
 
     def __init__(self, device: int = 0, hbm_budget_bytes: int = 0, variant: int = GD_VARIANT_AUTO,
                  smem_table_max: int | None = None, bitmap_max_outdeg: int | None = None,
-                 hub_wedges_log2: int | None = None):
+                 hub_wedges_log2: int | None = None, hub_pull: int | None = None):
         o = gd_default_options()
         o.variant = variant
+        if hub_pull is not None:
+            o.hub_pull = hub_pull
         if smem_table_max:
             o.smem_table_max = smem_table_max
         if bitmap_max_outdeg:

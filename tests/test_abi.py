@@ -41,6 +41,7 @@ def test_options_layout_and_defaults(lib):
     assert o.smem_table_max >= 256 and (o.smem_table_max & (o.smem_table_max - 1)) == 0
     assert ctypes.sizeof(gd.gd_options) == 48
     assert o.bitmap_max_outdeg == 1024 and o.hub_wedges_log2 == 17
+    assert o.hub_pull == gd.GD_PULL_AUTO
 
 
 def test_generators_are_deterministic_and_simple():

@@ -30,6 +30,11 @@ def ctxs():
     # the global-scratch 4-clique kernel for out-degrees above 8
     out["all_tiers"] = gd.Context(0, variant=gd.GD_VARIANT_ORIENTED, smem_table_max=256,
                                   bitmap_max_outdeg=8, hub_wedges_log2=6)
+    # global counts of every hub by per-node hub masks (pull form), or of none
+    out["pull_always"] = gd.Context(0, variant=gd.GD_VARIANT_ORIENTED, smem_table_max=256,
+                                    hub_wedges_log2=6, hub_pull=gd.GD_PULL_ALWAYS)
+    out["pull_never"] = gd.Context(0, variant=gd.GD_VARIANT_ORIENTED, smem_table_max=256,
+                                   hub_wedges_log2=6, hub_pull=gd.GD_PULL_NEVER)
     yield out
     for c in out.values():
         c.close()
@@ -68,7 +73,10 @@ def structured_graphs():
     return gs
 
 
-@pytest.mark.parametrize("variant", VARIANTS + ["tiny_table", "all_tiers"])
+ALL_CTX = VARIANTS + ["tiny_table", "all_tiers", "pull_always", "pull_never"]
+
+
+@pytest.mark.parametrize("variant", ALL_CTX)
 def test_tiny_graphs_match_bruteforce(ctxs, variant):
     for g in random_graphs(80, 11, 1):
         glob, pe = run_both(ctxs[variant], g)
@@ -77,7 +85,7 @@ def test_tiny_graphs_match_bruteforce(ctxs, variant):
         assert np.array_equal(pe, bf)
 
 
-@pytest.mark.parametrize("variant", VARIANTS + ["tiny_table", "all_tiers"])
+@pytest.mark.parametrize("variant", ALL_CTX)
 def test_structured_graphs_match_oracle(ctxs, variant):
     for g in structured_graphs():
         glob, pe = run_both(ctxs[variant], g)
@@ -85,7 +93,7 @@ def test_structured_graphs_match_oracle(ctxs, variant):
         assert np.array_equal(pe, oracle.o2_per_edge(g)), g.name
 
 
-@pytest.mark.parametrize("variant", VARIANTS + ["tiny_table", "all_tiers"])
+@pytest.mark.parametrize("variant", ALL_CTX)
 def test_medium_random_graphs(ctxs, variant):
     gs = [inputs.erdos_renyi(n, p, s) for s, (n, p) in enumerate([(257, 0.3), (1000, 0.02), (4099, 0.003)])]
     gs += [inputs.chung_lu(20_000, 2.2, 90_000, 0.0, 3), inputs.chung_lu(200_000, 2.05, 900_000, 0.0, 6)]
@@ -103,6 +111,19 @@ def test_erdos_renyi_workload_full(ctxs, variant):
     glob, pe = run_both(ctxs[variant], g)
     assert glob == oracle.alg2_global(g)
     assert np.array_equal(pe, oracle.alg2_per_edge(g))
+
+
+@pytest.mark.parametrize("mode", ["pull_always", "pull_never", gd.GD_VARIANT_ORIENTED])
+def test_bipartite_hubs_closed_form(ctxs, mode):
+    """Complete bipartite graphs K_{a,b} (Table 1 counts in closed form): the
+    b-side nodes are hubs whose masks are summed at the a-side nodes, whose
+    degrees reach the warp path and, for K_{2,300000}, the path for
+    degrees of 2^18 and more."""
+    from test_oracle_pins import closed_bipartite
+    for a, b in ((2, 300_000), (3, 70_000), (70, 1500)):
+        g = inputs.from_edges(a + b, [(i, a + j) for i in range(a) for j in range(b)])
+        with ctxs[mode].graph(g) as h:
+            assert h.count_global() == closed_bipartite(a, b), (a, b)
 
 
 def test_repeated_calls_identical(ctxs):
