@@ -125,7 +125,13 @@ typedef struct gd_options {
                                  has at least nnz/2 wedges, the rest by counter
                                  updates; GD_PULL_NEVER, GD_PULL_ALWAYS force one
                                  form for every hub (the counts are the same)      */
-    int32_t reserved[5];
+    int32_t batch_threads;    /* threads per CTA of the batched kernel (one graph
+                                 per CTA, its adjacency bit matrix in shared
+                                 memory): 0 (default) = 256 for graphs up to 512
+                                 nodes, 512 up to 1024; else 128, 256 or 512 for
+                                 the 512-node kernel and 256, 512 or 1024 for
+                                 the 1024-node kernel (the nearest is taken)  */
+    int32_t reserved[4];
 } gd_options;
 
 enum { GD_PULL_AUTO = 0, GD_PULL_NEVER = 1, GD_PULL_ALWAYS = 2 };
@@ -195,6 +201,26 @@ int gd_count_batch(gd_ctx *ctx, int32_t num_graphs, const int32_t *graph_node_pt
                    const int32_t *row_ptr, const int32_t *col_idx, int flags,
                    uint64_t *out);
 
+/* The counts of gd_count_batch for graphs that sit in device memory as
+ * separate CSRs (the collections of small graphs of Sec. 6, e.g. requests
+ * uploaded one by one): graph i has num_nodes[i] nodes and num_slots[i]
+ * stored entries, its row_ptr at row_ptrs[i] and its col_idx (local ids
+ * 0..n_i-1) at col_idxs[i].  row_ptrs and col_idxs are DEVICE arrays of
+ * num_graphs DEVICE pointers; num_nodes and num_slots are HOST arrays (the
+ * packed offsets are formed from them without a device round trip).  One
+ * gather kernel packs the graphs into one CSR (row offsets shifted by each
+ * graph's slot offset, ids by its node offset) held by the context; then the
+ * validation and the persistent counting launch of gd_count_batch run on it.
+ * out: DEVICE, num_graphs x 15 uint64.  flags: GD_CAPTURE records the gather,
+ * the validation and the count as one CUDA graph, replayed while the
+ * pointers and sizes stay the same (graphs of at most 1024 nodes).  Errors as
+ * gd_count_batch, plus GD_EINVAL when a graph's row_ptr does not start at 0
+ * or does not end at its slot count.  Runs on the context's stream;
+ * synchronous.  The caller keeps every array alive during the call. */
+int gd_count_batch_gather(gd_ctx *ctx, int32_t num_graphs, const int32_t *const *row_ptrs,
+                          const int32_t *const *col_idxs, const int32_t *num_nodes,
+                          const int64_t *num_slots, int flags, uint64_t *out);
+
 /* ------------------------------------------------------------------------
  * Measurement and memory hooks (no counterpart in the paper).
  * ------------------------------------------------------------------------ */
@@ -245,6 +271,14 @@ typedef struct gd_tune_result {
  * are identical under every option set; only the time differs. */
 int gd_autotune(gd_graph *g, int per_edge, int32_t max_trials, gd_tune_result *res);
 
+/* The same for the batched path (Sec. 6 collections): time gd_count_batch on
+ * this batch (arguments as gd_count_batch; out receives its counts) under
+ * every batch_threads value (host wall time of the synchronous call, best of
+ * two), and keep the fastest in the context's options; res->best.batch_threads
+ * is the choice.  Counts are identical under every value. */
+int gd_autotune_batch(gd_ctx *ctx, int32_t num_graphs, const int32_t *graph_node_ptr, const int32_t *row_ptr,
+                      const int32_t *col_idx, int flags, uint64_t *out, gd_tune_result *res);
+
 /* ------------------------------------------------------------------------
  * Serving: a request loop with continuous batching (no counterpart in the
  * paper; the counts of every request are those of gd_count_global).
@@ -266,16 +300,28 @@ typedef struct gd_req_stats {
     double submit_ms;          /* gd_submit returned                         */
     double start_ms;           /* a worker took it                           */
     double end_ms;             /* its counts were ready                      */
-    size_t footprint;          /* device bytes reserved for it at admission  */
+    size_t footprint;          /* device bytes reserved for it from admission
+                                  (CSR upload) to the end of its count        */
     int32_t slot;              /* worker that ran it                         */
     int32_t batched;           /* 1 if it ran inside a batched launch        */
 } gd_req_stats;
 
-/* Start the service of a context: `slots` worker threads, each with its own
- * CUDA stream and device-block cache, so their requests overlap on the GPU.
- * hbm_budget_bytes (0: the context's budget; 0 there too: unlimited) bounds
- * the sum of the estimated footprints of the requests running at once
- * (gd_footprint_estimate); a request waits until it fits.  gd_submit starts a
+/* A request that does not fit the budget may be passed by later requests
+ * that do, for at most this long after it was first passed at the head of
+ * the queue; then no other request is admitted until it fits. */
+#define GD_SERVE_MAX_BYPASS_MS 50.0
+
+/* Start the service of a context: a stager thread and `slots` worker
+ * threads, each worker with its own CUDA stream and device-block cache, so
+ * their requests overlap on the GPU.  hbm_budget_bytes (0: the context's
+ * budget; 0 there too: 45% of the device memory free at this call, the
+ * workers' block caches being kept within budget / slots each) bounds the
+ * sum of the estimated footprints of the admitted requests
+ * (gd_footprint_estimate); a request larger than it is refused by
+ * gd_submit with GD_ENOMEM.  The stager admits a
+ * request when it fits, reserving its footprint and uploading its CSR to the
+ * device, where it stays until the request's counts are done; workers count
+ * admitted requests straight from their device CSRs.  gd_submit starts a
  * service with 4 slots if none is running. */
 int gd_serve_start(gd_ctx *ctx, int32_t slots, size_t hbm_budget_bytes);
 

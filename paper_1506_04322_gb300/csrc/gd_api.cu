@@ -4,6 +4,8 @@
 // allocates, orders launches and reports errors.
 #include <cuda_runtime.h>
 
+#include <chrono>
+
 #include <algorithm>
 #include <cmath>
 #include <cstdarg>
@@ -201,7 +203,7 @@ int ensure_workspace(gd_graph *g, bool per_edge) {
     int rc;
     if (!w.status) {
         if ((rc = dalloc_n(g, &w.status, 4))) return rc;
-        GD_CK(g->ctx, cudaMemset(w.status, 0, 4 * sizeof(int32_t)));
+        GD_CK(g->ctx, cudaMemsetAsync(w.status, 0, 4 * sizeof(int32_t), g->stream));
     }
     std::vector<AllocSpec> sp;
     if (!w.first_up) {
@@ -214,7 +216,7 @@ int ensure_workspace(gd_graph *g, bool per_edge) {
         workspace_specs(w, n, m, nnz, w.wtab_ctas, 1, sp);
         if ((rc = alloc_specs(g, sp))) return rc;
         sp.clear();
-        GD_CK(g->ctx, cudaMemset(w.wtab, 0, sizeof(uint32_t) * (size_t)w.wtab_ctas * n));
+        GD_CK(g->ctx, cudaMemsetAsync(w.wtab, 0, sizeof(uint32_t) * (size_t)w.wtab_ctas * n, g->stream));
     }
     if (per_edge && !w.tnode) {
         workspace_specs(w, n, m, nnz, 0, 2, sp);
@@ -464,6 +466,8 @@ struct BatchGraph {
     int32_t G = 0, N = 0;
     int64_t nnz = 0;
     const void *gnp = nullptr, *rp = nullptr, *ci = nullptr;
+    const void *rps = nullptr, *cis = nullptr, *eoff = nullptr;   // gather step (gd_count_batch_gather)
+    std::vector<int32_t> eoff_host;
     void *out = nullptr;
     std::vector<int32_t> gnp_host;
     cudaGraph_t graph = nullptr;
@@ -509,6 +513,7 @@ static int check_options(gd_options *o) {
     if (o->bitmap_max_outdeg < 2 || o->bitmap_max_outdeg > gdi::CL_D2 || o->hub_wedges_log2 < 4 ||
         o->hub_wedges_log2 > 40) return GD_EINVAL;
     if (o->hub_pull < GD_PULL_AUTO || o->hub_pull > GD_PULL_ALWAYS) return GD_EINVAL;
+    if (o->batch_threads < 0 || o->batch_threads > 1024) return GD_EINVAL;
     return GD_OK;
 }
 
@@ -562,6 +567,15 @@ void gd_destroy(gd_ctx *ctx) {
     std::vector<gd_graph *> gs = ctx->graphs;
     for (gd_graph *g : gs) gd_destroy_graph(g);
     if (ctx->batch_buf) cudaFree(ctx->batch_buf);
+    {
+        gdi::GatherBufs &gb = ctx->gather;
+        if (gb.gnp) ctx_release(ctx, gb.gnp, gb.gnp_bytes);
+        if (gb.eoff) ctx_release(ctx, gb.eoff, gb.eoff_bytes);
+        if (gb.rp) ctx_release(ctx, gb.rp, gb.rp_bytes);
+        if (gb.ci) ctx_release(ctx, gb.ci, gb.ci_bytes);
+        if (gb.misc) ctx_release(ctx, gb.misc, gb.misc_bytes);
+        gb = gdi::GatherBufs();
+    }
     trim_pool(ctx);
     for (auto &r : ctx->recs) { ctx->evpool.push_back(r.a); ctx->evpool.push_back(r.b); }
     for (cudaEvent_t ev : ctx->evpool) cudaEventDestroy(ev);
@@ -798,16 +812,20 @@ struct PoolBlocks {
     ~PoolBlocks() { for (auto &b : bl) ctx_release(ctx, b.first, b.second); }
 };
 
-// The device part of a batch call as a captured CUDA graph: zero the work
-// words, validate the packed union, count (one persistent launch), copy the
-// status words to pinned host memory.  Replayed while the call is the same.
+// The device part of a batch call as a captured CUDA graph: (gather the
+// per-graph CSRs into the packed arrays,) zero the work words, validate the
+// packed union, count (one persistent launch), copy the status words to
+// pinned host memory.  Replayed while the call is the same.
 static int count_batch_captured(gd_ctx *ctx, int32_t G, const std::vector<int32_t> &gnp, int32_t N, int64_t nnz,
                                 int32_t nmax_graph, const int32_t *d_gnp, const int32_t *d_rp, const int32_t *d_ci,
-                                uint64_t *d_out) {
+                                uint64_t *d_out, const int32_t *const *rps = nullptr,
+                                const int32_t *const *cis = nullptr, const int32_t *d_eoff = nullptr,
+                                const std::vector<int32_t> *eoff = nullptr) {
     cudaStream_t st = ctx->stream;
     BatchGraph *b = ctx->bgraph;
     const bool same = b && b->G == G && b->N == N && b->nnz == nnz && b->gnp == d_gnp && b->rp == d_rp &&
-                      b->ci == d_ci && b->out == d_out && b->gnp_host == gnp;
+                      b->ci == d_ci && b->out == d_out && b->gnp_host == gnp && b->rps == (const void *)rps &&
+                      b->cis == (const void *)cis && b->eoff == d_eoff && (!eoff || b->eoff_host == *eoff);
     if (!same) {
         batch_graph_destroy(ctx);
         b = new (std::nothrow) BatchGraph();
@@ -815,6 +833,8 @@ static int count_batch_captured(gd_ctx *ctx, int32_t G, const std::vector<int32_
         ctx->bgraph = b;
         b->G = G; b->N = N; b->nnz = nnz; b->gnp = d_gnp; b->rp = d_rp; b->ci = d_ci; b->out = d_out;
         b->gnp_host = gnp;
+        b->rps = rps; b->cis = cis; b->eoff = d_eoff;
+        if (eoff) b->eoff_host = *eoff;
         b->misc_bytes = 64 * sizeof(int32_t);
         b->big_bytes = sizeof(int32_t) * (size_t)G;
         int rc;
@@ -828,12 +848,15 @@ static int count_batch_captured(gd_ctx *ctx, int32_t G, const std::vector<int32_
         ctx->prof = false;      // no event records inside the capture
         cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) e = cudaMemsetAsync(b->d_misc, 0, b->misc_bytes, st);
+        if (e == cudaSuccess && rps)
+            e = launch_batch_gather(ctx, st, G, rps, cis, d_gnp, d_eoff, const_cast<int32_t *>(d_rp),
+                                    const_cast<int32_t *>(d_ci), b->d_misc + 16);
         if (e == cudaSuccess) e = launch_validate(&tmp, b->d_misc + 8);
         if (e == cudaSuccess)
             e = launch_batch_count(ctx, st, G, d_gnp, d_rp, d_ci, b->d_misc, (unsigned long long *)d_out,
                                    b->d_misc + 1, b->d_big, b->d_misc + 2, nmax_graph <= 512 ? 512 : 1024);
         if (e == cudaSuccess)
-            e = cudaMemcpyAsync(b->h_status, b->d_misc, 16 * sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+            e = cudaMemcpyAsync(b->h_status, b->d_misc, 20 * sizeof(int32_t), cudaMemcpyDeviceToHost, st);
         cudaGraph_t graph = nullptr;
         cudaError_t e2 = cudaStreamEndCapture(st, &graph);
         ctx->prof = prof;
@@ -847,11 +870,83 @@ static int count_batch_captured(gd_ctx *ctx, int32_t G, const std::vector<int32_
     GD_CK(ctx, cudaGraphLaunch(b->exec, st));
     GD_CK(ctx, cudaStreamSynchronize(st));
     const int32_t *h = b->h_status;
+    if (rps && h[16])
+        return fail(ctx, GD_EINVAL, "a graph's row_ptr does not start at 0 or does not end at its slot count");
     if (h[8] || h[10] != h[11])
         return fail(ctx, GD_EINVAL, "invalid batch CSR: rows must be strictly ascending, ids in range, "
                     "no self-loops, every edge stored in both directions");
     if (h[1] & 1) return fail(ctx, GD_EINVAL, "an edge of the batch leaves its graph's node range");
     if (h[1]) return fail(ctx, GD_EARITH, "inconsistent batch counts (status 0x%x)", h[1]);
+    return GD_OK;
+}
+
+// Validate and count a packed batch already on the device (the union CSR
+// d_rp / d_ci with graph offsets d_gnp; host copy gnp), rows of 15 counts to
+// d_out; graphs above the shared-memory limit go through the single-graph
+// path on a relabelled copy.
+static int count_packed(gd_ctx *ctx, int32_t num_graphs, const std::vector<int32_t> &gnp, int32_t N, int64_t nnz,
+                        int32_t nmax_graph, const int32_t *d_gnp, const int32_t *d_rp, const int32_t *d_ci,
+                        unsigned long long *d_out, PoolBlocks &pb) {
+    cudaStream_t st = ctx->stream;
+    int rc;
+    int32_t *d_misc;    // [0] work index, [1] status, [2] big count, [3..6] validate status
+    int32_t *d_big;
+    if ((rc = pb.get((void **)&d_misc, 64 * sizeof(int32_t)))) return rc;
+    if ((rc = pb.get((void **)&d_big, sizeof(int32_t) * (size_t)num_graphs))) return rc;
+    // validate the packed union (rows sorted, ids in range, no self-loops, symmetric)
+    {
+        gd_graph tmp;
+        tmp.ctx = ctx; tmp.stream = st; tmp.n = N; tmp.nnz = nnz; tmp.m = nnz / 2;
+        tmp.rp = const_cast<int32_t *>(d_rp); tmp.ci = const_cast<int32_t *>(d_ci);
+        tmp.ws.status = d_misc + 8;
+        int32_t bad_index = -1, bad_code = 0;
+        GD_CK(ctx, validate_csr(&tmp, &bad_index, &bad_code));
+        tmp.ws = Workspace();
+        if (bad_code)
+            return fail(ctx, GD_EINVAL, "invalid batch CSR at row %d: rows must be strictly ascending, ids in range, "
+                        "no self-loops, every edge stored in both directions", bad_index);
+    }
+    GD_CK(ctx, cudaMemsetAsync(d_misc, 0, 8 * sizeof(int32_t), st));
+    const int nmax = nmax_graph <= 512 ? 512 : 1024;
+    GD_CK(ctx, launch_batch_count(ctx, st, num_graphs, d_gnp, d_rp, d_ci, d_misc, d_out, d_misc + 1, d_big,
+                                  d_misc + 2, nmax));
+    int32_t misc[3];
+    GD_CK(ctx, cudaMemcpyAsync(misc, d_misc, sizeof(misc), cudaMemcpyDeviceToHost, st));
+    GD_CK(ctx, cudaStreamSynchronize(st));
+    if (misc[1] & 1) return fail(ctx, GD_EINVAL, "an edge of the batch leaves its graph's node range");
+    if (misc[1]) return fail(ctx, GD_EARITH, "inconsistent batch counts (status 0x%x)", misc[1]);
+    // graphs above the shared-memory limit: the single-graph path on a relabelled copy
+    if (misc[2] > 0) {
+        std::vector<int32_t> big((size_t)misc[2]);
+        GD_CK(ctx, cudaMemcpyAsync(big.data(), d_big, sizeof(int32_t) * big.size(), cudaMemcpyDeviceToHost, st));
+        GD_CK(ctx, cudaStreamSynchronize(st));
+        for (int32_t gi : big) {
+            const int32_t n0 = gnp[gi], n = gnp[gi + 1] - gnp[gi];
+            int32_t ends[2];
+            GD_CK(ctx, cudaMemcpyAsync(ends, d_rp + n0, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+            GD_CK(ctx, cudaMemcpyAsync(ends + 1, d_rp + n0 + n, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+            GD_CK(ctx, cudaStreamSynchronize(st));
+            const int64_t ne = ends[1] - ends[0];
+            PoolBlocks lb(ctx);
+            int32_t *lrp, *lci;
+            if ((rc = lb.get((void **)&lrp, sizeof(int32_t) * ((size_t)n + 1)))) return rc;
+            if ((rc = lb.get((void **)&lci, sizeof(int32_t) * (size_t)std::max<int64_t>(ne, 1)))) return rc;
+            GD_CK(ctx, launch_batch_slice(ctx, st, n0, n, d_rp, d_ci, lrp, lci));
+            gd_graph *sub = nullptr;
+            if ((rc = gd_create_csr(ctx, n, ne, lrp, lci, GD_DEVICE_PTRS | GD_BORROW, st, &sub))) return rc;
+            gd_u128 r[15];
+            rc = gd_count_global(sub, r);
+            gd_destroy_graph(sub);
+            if (rc) return rc;
+            uint64_t row[15];
+            for (int k = 0; k < 15; k++) {
+                if (r[k].hi) return fail(ctx, GD_EOVERFLOW, "graph %d: a count exceeds uint64", gi);
+                row[k] = r[k].lo;
+            }
+            GD_CK(ctx, cudaMemcpyAsync(d_out + (size_t)gi * 15, row, sizeof(row), cudaMemcpyHostToDevice, st));
+            GD_CK(ctx, cudaStreamSynchronize(st));
+        }
+    }
     return GD_OK;
 }
 
@@ -916,67 +1011,75 @@ int gd_count_batch(gd_ctx *ctx, int32_t num_graphs, const int32_t *graph_node_pt
     if (!dev_out) {
         if ((rc = pb.get((void **)&d_out, sizeof(uint64_t) * 15 * (size_t)num_graphs))) return rc;
     }
-    int32_t *d_misc;    // [0] work index, [1] status, [2] big count, [3..6] validate status
-    int32_t *d_big;
-    if ((rc = pb.get((void **)&d_misc, 64 * sizeof(int32_t)))) return rc;
-    if ((rc = pb.get((void **)&d_big, sizeof(int32_t) * (size_t)num_graphs))) return rc;
-    // validate the packed union (rows sorted, ids in range, no self-loops, symmetric)
-    {
-        gd_graph tmp;
-        tmp.ctx = ctx; tmp.stream = st; tmp.n = N; tmp.nnz = nnz; tmp.m = nnz / 2;
-        tmp.rp = const_cast<int32_t *>(d_rp); tmp.ci = const_cast<int32_t *>(d_ci);
-        tmp.ws.status = d_misc + 8;
-        int32_t bad_index = -1, bad_code = 0;
-        GD_CK(ctx, validate_csr(&tmp, &bad_index, &bad_code));
-        tmp.ws = Workspace();
-        if (bad_code)
-            return fail(ctx, GD_EINVAL, "invalid batch CSR at row %d: rows must be strictly ascending, ids in range, "
-                        "no self-loops, every edge stored in both directions", bad_index);
-    }
-    GD_CK(ctx, cudaMemsetAsync(d_misc, 0, 8 * sizeof(int32_t), st));
-    const int nmax = nmax_graph <= 512 ? 512 : 1024;
-    GD_CK(ctx, launch_batch_count(ctx, st, num_graphs, d_gnp, d_rp, d_ci, d_misc, d_out, d_misc + 1, d_big,
-                                  d_misc + 2, nmax));
-    int32_t misc[3];
-    GD_CK(ctx, cudaMemcpyAsync(misc, d_misc, sizeof(misc), cudaMemcpyDeviceToHost, st));
-    GD_CK(ctx, cudaStreamSynchronize(st));
-    if (misc[1] & 1) return fail(ctx, GD_EINVAL, "an edge of the batch leaves its graph's node range");
-    if (misc[1]) return fail(ctx, GD_EARITH, "inconsistent batch counts (status 0x%x)", misc[1]);
-    // graphs above the shared-memory limit: the single-graph path on a relabelled copy
-    if (misc[2] > 0) {
-        std::vector<int32_t> big((size_t)misc[2]);
-        GD_CK(ctx, cudaMemcpyAsync(big.data(), d_big, sizeof(int32_t) * big.size(), cudaMemcpyDeviceToHost, st));
-        GD_CK(ctx, cudaStreamSynchronize(st));
-        for (int32_t gi : big) {
-            const int32_t n0 = gnp[gi], n = gnp[gi + 1] - gnp[gi];
-            int32_t ends[2];
-            GD_CK(ctx, cudaMemcpyAsync(ends, d_rp + n0, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-            GD_CK(ctx, cudaMemcpyAsync(ends + 1, d_rp + n0 + n, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-            GD_CK(ctx, cudaStreamSynchronize(st));
-            const int64_t ne = ends[1] - ends[0];
-            PoolBlocks lb(ctx);
-            int32_t *lrp, *lci;
-            if ((rc = lb.get((void **)&lrp, sizeof(int32_t) * ((size_t)n + 1)))) return rc;
-            if ((rc = lb.get((void **)&lci, sizeof(int32_t) * (size_t)std::max<int64_t>(ne, 1)))) return rc;
-            GD_CK(ctx, launch_batch_slice(ctx, st, n0, n, d_rp, d_ci, lrp, lci));
-            gd_graph *sub = nullptr;
-            if ((rc = gd_create_csr(ctx, n, ne, lrp, lci, GD_DEVICE_PTRS | GD_BORROW, st, &sub))) return rc;
-            gd_u128 r[15];
-            rc = gd_count_global(sub, r);
-            gd_destroy_graph(sub);
-            if (rc) return rc;
-            uint64_t row[15];
-            for (int k = 0; k < 15; k++) {
-                if (r[k].hi) return fail(ctx, GD_EOVERFLOW, "graph %d: a count exceeds uint64", gi);
-                row[k] = r[k].lo;
-            }
-            GD_CK(ctx, cudaMemcpyAsync(d_out + (size_t)gi * 15, row, sizeof(row), cudaMemcpyHostToDevice, st));
-            GD_CK(ctx, cudaStreamSynchronize(st));
-        }
-    }
+    if ((rc = count_packed(ctx, num_graphs, gnp, N, nnz, nmax_graph, d_gnp, d_rp, d_ci, d_out, pb))) return rc;
     if (!dev_out) {
         GD_CK(ctx, cudaMemcpyAsync(out, d_out, sizeof(uint64_t) * 15 * (size_t)num_graphs, cudaMemcpyDeviceToHost, st));
     }
+    GD_CK(ctx, cudaStreamSynchronize(st));
+    return GD_OK;
+}
+
+int gd_count_batch_gather(gd_ctx *ctx, int32_t num_graphs, const int32_t *const *row_ptrs,
+                          const int32_t *const *col_idxs, const int32_t *num_nodes, const int64_t *num_slots,
+                          int flags, uint64_t *out) {
+    if (!ctx) return GD_EINVAL;
+    ctx->err.clear();
+    if (num_graphs < 0 || (num_graphs > 0 && (!row_ptrs || !col_idxs || !num_nodes || !num_slots || !out)))
+        return fail(ctx, GD_EINVAL, "gd_count_batch_gather: null pointer or negative graph count");
+    GD_CK(ctx, cudaSetDevice(ctx->device));
+    if (num_graphs == 0) return GD_OK;
+    cudaStream_t st = ctx->stream;
+    // node and slot offsets of the packed batch, from the host sizes
+    std::vector<int32_t> gnp((size_t)num_graphs + 1), eoff((size_t)num_graphs + 1);
+    int64_t N = 0, E = 0;
+    int32_t nmax_graph = 0;
+    for (int32_t i = 0; i < num_graphs; i++) {
+        const int32_t n = num_nodes[i];
+        const int64_t e = num_slots[i];
+        if (n < 0 || e < 0 || (e & 1))
+            return fail(ctx, GD_EINVAL, "graph %d: negative size or odd slot count", i);
+        gnp[i] = (int32_t)N;
+        eoff[i] = (int32_t)E;
+        N += n;
+        E += e;
+        if (N > INT32_MAX - 1 || E > INT32_MAX)
+            return fail(ctx, GD_EOVERFLOW, "the packed batch exceeds int32 node or slot indices");
+        nmax_graph = std::max(nmax_graph, n);
+    }
+    gnp[num_graphs] = (int32_t)N;
+    eoff[num_graphs] = (int32_t)E;
+    if (nmax_graph > 65535)
+        return fail(ctx, GD_EOVERFLOW, "a graph of the batch has %d nodes; per-graph uint64 counts need <= 65535",
+                    nmax_graph);
+    // packed arrays, kept by the context for the next call of the same shape
+    GatherBufs &gb = ctx->gather;
+    int rc;
+    auto grow = [&](void **p, size_t &cap, size_t need) -> int {
+        if (*p && cap >= need) return GD_OK;
+        if (*p) { ctx_release(ctx, *p, cap); *p = nullptr; cap = 0; }
+        int r = ctx_alloc(ctx, p, need);
+        if (r == GD_OK) cap = need;
+        return r;
+    };
+    if ((rc = grow((void **)&gb.gnp, gb.gnp_bytes, sizeof(int32_t) * gnp.size()))) return rc;
+    if ((rc = grow((void **)&gb.eoff, gb.eoff_bytes, sizeof(int32_t) * eoff.size()))) return rc;
+    if ((rc = grow((void **)&gb.rp, gb.rp_bytes, sizeof(int32_t) * (size_t)(N + 1)))) return rc;
+    if ((rc = grow((void **)&gb.ci, gb.ci_bytes, sizeof(int32_t) * (size_t)std::max<int64_t>(E, 1)))) return rc;
+    if ((rc = grow((void **)&gb.misc, gb.misc_bytes, 64 * sizeof(int32_t)))) return rc;
+    GD_CK(ctx, cudaMemcpyAsync(gb.gnp, gnp.data(), sizeof(int32_t) * gnp.size(), cudaMemcpyHostToDevice, st));
+    GD_CK(ctx, cudaMemcpyAsync(gb.eoff, eoff.data(), sizeof(int32_t) * eoff.size(), cudaMemcpyHostToDevice, st));
+    if ((flags & GD_CAPTURE) && nmax_graph <= 1024)
+        return count_batch_captured(ctx, num_graphs, gnp, (int32_t)N, E, nmax_graph, gb.gnp, gb.rp, gb.ci, out,
+                                    row_ptrs, col_idxs, gb.eoff, &eoff);
+    GD_CK(ctx, cudaMemsetAsync(gb.misc, 0, sizeof(int32_t), st));
+    GD_CK(ctx, launch_batch_gather(ctx, st, num_graphs, row_ptrs, col_idxs, gb.gnp, gb.eoff, gb.rp, gb.ci, gb.misc));
+    int32_t gstat = 0;
+    GD_CK(ctx, cudaMemcpyAsync(&gstat, gb.misc, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    GD_CK(ctx, cudaStreamSynchronize(st));
+    if (gstat) return fail(ctx, GD_EINVAL, "a graph's row_ptr does not start at 0 or does not end at its slot count");
+    PoolBlocks pb(ctx);
+    if ((rc = count_packed(ctx, num_graphs, gnp, (int32_t)N, E, nmax_graph, gb.gnp, gb.rp, gb.ci,
+                           (unsigned long long *)out, pb))) return rc;
     GD_CK(ctx, cudaStreamSynchronize(st));
     return GD_OK;
 }
@@ -1039,6 +1142,46 @@ int gd_autotune(gd_graph *g, int per_edge, int32_t max_trials, gd_tune_result *r
             }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    ctx->opt = best;
+    res->best = best;
+    res->best_ms = best_ms;
+    res->trials = trials;
+    return GD_OK;
+}
+
+int gd_autotune_batch(gd_ctx *ctx, int32_t num_graphs, const int32_t *graph_node_ptr, const int32_t *row_ptr,
+                      const int32_t *col_idx, int flags, uint64_t *out, gd_tune_result *res) {
+    if (!ctx || !res) return GD_EINVAL;
+    memset(res, 0, sizeof(*res));
+    const gd_options start = ctx->opt;
+    using clk = std::chrono::steady_clock;
+    auto time_once = [&](double *ms) -> int {
+        double best = 1e30;
+        for (int r = 0; r < 2; r++) {
+            const auto t0 = clk::now();
+            int rc = gd_count_batch(ctx, num_graphs, graph_node_ptr, row_ptr, col_idx, flags & ~GD_CAPTURE, out);
+            if (rc) return rc;
+            best = std::min(best, std::chrono::duration<double, std::milli>(clk::now() - t0).count());
+        }
+        *ms = best;
+        return GD_OK;
+    };
+    double best_ms = 0;
+    int rc = time_once(&best_ms);
+    if (rc) { ctx->opt = start; return rc; }
+    res->default_ms = best_ms;
+    gd_options best = start;
+    int32_t trials = 1;
+    for (int32_t t : {128, 256, 512, 1024}) {
+        if (t == start.batch_threads) continue;
+        gd_options o = start;
+        o.batch_threads = t;
+        ctx->opt = o;
+        double ms = 0;
+        if ((rc = time_once(&ms))) { ctx->opt = start; return rc; }
+        trials++;
+        if (ms < best_ms) { best_ms = ms; best = o; }
+    }
     ctx->opt = best;
     res->best = best;
     res->best_ms = best_ms;

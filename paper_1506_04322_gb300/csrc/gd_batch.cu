@@ -15,6 +15,8 @@
 //   Step 4  the Lemmas of Sec. 4.3 (exact u128), one result row per graph.
 // Graphs with more than NMAX nodes are counted by the single-graph path.
 #include <cuda_runtime.h>
+
+#include <algorithm>
 #include <stdint.h>
 
 #include "gd_device.cuh"
@@ -178,34 +180,87 @@ __global__ void k_batch_slice(int32_t n0, int32_t n, const int32_t *__restrict__
         lci[p] = ci[e0 + p] - n0;
 }
 
+// Gather graphs held as separate device CSRs into one packed batch: a warp
+// per graph copies its row offsets shifted by the graph's slot offset and
+// its neighbour ids shifted by its node offset.  Graph i's row_ptr must
+// start at 0 and end at its slot count; otherwise bit BERR_EDGE of the
+// status is set and the graph's rows are left empty (the packed CSR stays
+// well formed and the call is refused afterwards).
+__global__ void k_batch_gather(int32_t num_graphs, const int32_t *const *__restrict__ rps,
+                               const int32_t *const *__restrict__ cis, const int32_t *__restrict__ gnp,
+                               const int32_t *__restrict__ eoff, int32_t *rp_out, int32_t *ci_out,
+                               int32_t *gstatus) {
+    const int lane = lane_id();
+    for (int64_t i = global_warp(); i < num_graphs; i += num_warps()) {
+        const int32_t n0 = gnp[i], n = gnp[i + 1] - n0;
+        const int32_t e0 = eoff[i], ne = eoff[i + 1] - e0;
+        const int32_t *rp = rps[i];
+        const int32_t *ci = cis[i];
+        const bool ok = n == 0 ? true : (rp[0] == 0 && rp[n] == ne);
+        if (!ok) {
+            if (lane == 0) atomicOr(gstatus, BERR_EDGE);
+            for (int32_t u = lane; u < n; u += WARP) rp_out[n0 + u] = e0;
+            for (int32_t p = lane; p < ne; p += WARP) ci_out[e0 + p] = n0;
+            continue;
+        }
+        for (int32_t u = lane; u < n; u += WARP) rp_out[n0 + u] = e0 + rp[u];
+        for (int32_t p = lane; p < ne; p += WARP) ci_out[e0 + p] = n0 + ci[p];
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) rp_out[gnp[num_graphs]] = eoff[num_graphs];
+}
+
 }  // namespace
 
 size_t batch_smem_bytes(int nmax) { return (size_t)nmax * (nmax / 32 + 1) * 4; }
 
+template <int NMAX, int THREADS>
+static cudaError_t launch_bitmatrix(gd_graph *g, int32_t num_graphs, const int32_t *gnp, const int32_t *rp,
+                                    const int32_t *ci, int32_t *work, unsigned long long *out, int32_t *gstatus,
+                                    int32_t *big_list, int32_t *big_count) {
+    cudaError_t e;
+    int per_sm = 0;
+    const size_t smem = batch_smem_bytes(NMAX);
+    if ((e = cudaFuncSetAttribute(k_batch_bitmatrix<NMAX, THREADS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_bitmatrix<NMAX, THREADS>, THREADS, smem))) return e;
+    const int grid = g->ctx->num_sms * (per_sm > 0 ? per_sm : 1);
+    GD_LAUNCH(g, "k_batch_bitmatrix", (k_batch_bitmatrix<NMAX, THREADS>), (unsigned)grid, THREADS, smem,
+              num_graphs, gnp, rp, ci, work, out, gstatus, big_list, big_count);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_batch_count(gd_ctx *ctx, cudaStream_t st, int32_t num_graphs, const int32_t *gnp,
                                const int32_t *rp, const int32_t *ci, int32_t *work, unsigned long long *out,
                                int32_t *gstatus, int32_t *big_list, int32_t *big_count, int nmax) {
-    cudaError_t e;
     gd_graph tmp;     // carrier for the launch macro (context + stream)
     tmp.ctx = ctx;
     tmp.stream = st;
     gd_graph *g = &tmp;
-    int per_sm = 0;
+    const int t = ctx->opt.batch_threads;
     if (nmax == 512) {
-        const size_t smem = batch_smem_bytes(512);
-        if ((e = cudaFuncSetAttribute(k_batch_bitmatrix<512, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))) return e;
-        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_bitmatrix<512, 256>, 256, smem))) return e;
-        const int grid = ctx->num_sms * (per_sm > 0 ? per_sm : 1);
-        GD_LAUNCH(g, "k_batch_bitmatrix", (k_batch_bitmatrix<512, 256>), (unsigned)grid, 256, smem,
-                  num_graphs, gnp, rp, ci, work, out, gstatus, big_list, big_count);
-    } else {
-        const size_t smem = batch_smem_bytes(1024);
-        if ((e = cudaFuncSetAttribute(k_batch_bitmatrix<1024, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))) return e;
-        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_bitmatrix<1024, 512>, 512, smem))) return e;
-        const int grid = ctx->num_sms * (per_sm > 0 ? per_sm : 1);
-        GD_LAUNCH(g, "k_batch_bitmatrix", (k_batch_bitmatrix<1024, 512>), (unsigned)grid, 512, smem,
-                  num_graphs, gnp, rp, ci, work, out, gstatus, big_list, big_count);
+        if (t > 0 && t <= 192)
+            return launch_bitmatrix<512, 128>(g, num_graphs, gnp, rp, ci, work, out, gstatus, big_list, big_count);
+        if (t > 384)
+            return launch_bitmatrix<512, 512>(g, num_graphs, gnp, rp, ci, work, out, gstatus, big_list, big_count);
+        return launch_bitmatrix<512, 256>(g, num_graphs, gnp, rp, ci, work, out, gstatus, big_list, big_count);
     }
+    if (t > 0 && t <= 384)
+        return launch_bitmatrix<1024, 256>(g, num_graphs, gnp, rp, ci, work, out, gstatus, big_list, big_count);
+    if (t > 768)
+        return launch_bitmatrix<1024, 1024>(g, num_graphs, gnp, rp, ci, work, out, gstatus, big_list, big_count);
+    return launch_bitmatrix<1024, 512>(g, num_graphs, gnp, rp, ci, work, out, gstatus, big_list, big_count);
+}
+
+cudaError_t launch_batch_gather(gd_ctx *ctx, cudaStream_t st, int32_t num_graphs, const int32_t *const *rps,
+                                const int32_t *const *cis, const int32_t *gnp, const int32_t *eoff,
+                                int32_t *rp_out, int32_t *ci_out, int32_t *gstatus) {
+    gd_graph tmp;
+    tmp.ctx = ctx;
+    tmp.stream = st;
+    gd_graph *g = &tmp;
+    const int64_t warps = std::max<int32_t>(num_graphs, 1);
+    const unsigned grid = (unsigned)std::min<int64_t>((warps * 32 + 255) / 256, (int64_t)ctx->num_sms * 8);
+    GD_LAUNCH(g, "k_batch_gather", k_batch_gather, grid, 256, 0, num_graphs, rps, cis, gnp, eoff, rp_out, ci_out,
+              gstatus);
     return cudaGetLastError();
 }
 

@@ -145,6 +145,14 @@ struct ProfRec {
 }  // namespace gdi
 
 
+namespace gdi {
+// packed arrays of gd_count_batch_gather (grown on demand, kept for reuse)
+struct GatherBufs {
+    int32_t *gnp = nullptr, *eoff = nullptr, *rp = nullptr, *ci = nullptr, *misc = nullptr;
+    size_t gnp_bytes = 0, eoff_bytes = 0, rp_bytes = 0, ci_bytes = 0, misc_bytes = 0;
+};
+}  // namespace gdi
+
 struct gd_ctx {
     int device = 0;
     size_t budget = 0;           // 0 = unlimited
@@ -169,6 +177,7 @@ struct gd_ctx {
     gdi::Service *service = nullptr;
     // captured batch pipeline
     gdi::BatchGraph *bgraph = nullptr;
+    gdi::GatherBufs gather;
 };
 
 struct gd_graph {
@@ -234,6 +243,9 @@ size_t batch_smem_bytes(int nmax);
 cudaError_t launch_batch_count(gd_ctx *ctx, cudaStream_t st, int32_t num_graphs, const int32_t *gnp,
                                const int32_t *rp, const int32_t *ci, int32_t *work, unsigned long long *out,
                                int32_t *gstatus, int32_t *big_list, int32_t *big_count, int nmax);
+cudaError_t launch_batch_gather(gd_ctx *ctx, cudaStream_t st, int32_t num_graphs, const int32_t *const *rps,
+                                const int32_t *const *cis, const int32_t *gnp, const int32_t *eoff,
+                                int32_t *rp_out, int32_t *ci_out, int32_t *gstatus);
 cudaError_t launch_batch_slice(gd_ctx *ctx, cudaStream_t st, int32_t n0, int32_t n, const int32_t *rp,
                                const int32_t *ci, int32_t *lrp, int32_t *lci);
 

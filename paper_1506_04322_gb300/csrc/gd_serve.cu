@@ -1,18 +1,26 @@
 // gd_serve.cu -- the request loop: counting requests of mixed graph sizes are
 // submitted as they arrive (gd_submit), admitted by device-memory footprint,
-// run concurrently on the GPU, and collected with gd_poll.  Host code only.
+// kept resident on the device, run concurrently on the GPU, and collected
+// with gd_poll.  Host code only.
 //
-// A service owns `slots` worker threads.  Each worker has its own libgd
-// context (its own CUDA stream, its own block cache), so the requests it runs
-// overlap on the device with the other workers' requests.  A worker takes the
-// oldest queued request whose estimated footprint fits in what the budget has
-// left; a small request (a graph that fits the batched kernel) takes every
-// other queued small request that fits with it and runs them as one batched
-// launch (continuous batching: requests that arrived while the GPU was busy
-// ride along in the next launch).  A request larger than the whole budget is
-// refused at submission with GD_ENOMEM.
+// A service owns a stager thread and `slots` worker threads.  The stager
+// admits requests in arrival order as the budget allows: it reserves a
+// request's estimated footprint and uploads its CSR to the device on its own
+// stream, so the CSR stays resident from admission until the counts are
+// done.  A request that does not fit yet may be passed by later ones that
+// do, but once it has waited GD_SERVE_MAX_BYPASS_MS at the head of the
+// queue, nothing else is admitted until it fits (no starvation).  Each
+// worker has its own libgd context (its own CUDA stream, its own block
+// cache), so the requests it runs overlap on the device with the other
+// workers' requests.  A worker takes the oldest admitted request; a small one
+// (a graph that fits the batched kernel) takes every other admitted small
+// request with it and counts them in one batched launch straight from their
+// device CSRs (continuous batching: requests that arrived while the GPU was
+// busy ride along in the next launch).  A request larger than the whole
+// budget is refused at submission with GD_ENOMEM.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -36,12 +44,14 @@ struct Request {
     gd_req id = 0;
     int32_t n = 0;
     int64_t nnz = 0;
-    std::vector<int32_t> rp, ci;
+    std::vector<int32_t> rp, ci;          // host copy until the upload at admission
+    int32_t *d_rp = nullptr, *d_ci = nullptr;   // device CSR, admission to completion
     size_t footprint = 0;
-    int state = 0;            // 0 queued, 1 running, 2 done
+    int state = 0;            // 0 queued, 3 admitted (resident), 1 running, 2 done
     int status = GD_OK;
     gd_u128 result[15];
     double t_submit = 0, t_start = 0, t_end = 0;
+    double t_passed = -1;     // first time it was passed over at the head of the queue
     int32_t slot = -1, batched = 0;
 };
 
@@ -55,8 +65,12 @@ struct Service {
     std::vector<gd_ctx *> sub;
     std::vector<std::thread> workers;
     std::mutex mu;
-    std::condition_variable cv_work, cv_done;
-    std::deque<Request *> queue;
+    std::condition_variable cv_work, cv_done, cv_admit;
+    std::deque<Request *> queue;       // submitted, waiting for admission
+    std::deque<Request *> admitted;    // footprint reserved, CSR on the device
+    std::thread stager;
+    cudaStream_t stage_stream = nullptr;
+    double max_bypass_ms = GD_SERVE_MAX_BYPASS_MS;
     std::unordered_map<gd_req, Request *> all;
     gd_req next_id = 1;
     bool stop = false;
@@ -72,26 +86,93 @@ struct Service {
 
 namespace {
 
-// Take work for one worker: the oldest fitting request, plus fitting small
-// requests to batch with it.  Called with the lock held.
-bool pick(Service *s, std::vector<Request *> &out) {
-    out.clear();
-    for (auto it = s->queue.begin(); it != s->queue.end(); ++it) {
+// Admission (stager, lock held): the oldest queued request if it fits; else
+// a later one that fits, unless the oldest has waited max_bypass_ms since it
+// was first passed over -- then nothing until it fits.
+Request *admit(Service *s) {
+    if (s->queue.empty()) return nullptr;
+    Request *head = s->queue.front();
+    if (s->fits(head->footprint)) {
+        s->queue.pop_front();
+        s->inflight += head->footprint;
+        return head;
+    }
+    const double t = s->now_ms();
+    if (head->t_passed < 0) head->t_passed = t;
+    if (t - head->t_passed >= s->max_bypass_ms) return nullptr;
+    for (auto it = s->queue.begin() + 1; it != s->queue.end(); ++it) {
         Request *r = *it;
         if (!s->fits(r->footprint)) continue;
-        out.push_back(r);
-        s->inflight += r->footprint;
         s->queue.erase(it);
-        break;
+        s->inflight += r->footprint;
+        return r;
     }
-    if (out.empty()) return false;
+    return nullptr;
+}
+
+// Upload an admitted request's CSR on the stager's stream (stream-ordered
+// allocation: no device-wide synchronization while workers count).
+int stage(Service *s, Request *r) {
+    cudaStream_t st = s->stage_stream;
+    const size_t rb = sizeof(int32_t) * ((size_t)r->n + 1), cb = sizeof(int32_t) * (size_t)std::max<int64_t>(r->nnz, 1);
+    cudaError_t e = cudaMallocAsync((void **)&r->d_rp, rb, st);
+    if (e == cudaSuccess) e = cudaMallocAsync((void **)&r->d_ci, cb, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(r->d_rp, r->rp.data(), rb, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && r->nnz > 0)
+        e = cudaMemcpyAsync(r->d_ci, r->ci.data(), sizeof(int32_t) * (size_t)r->nnz, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? GD_ENOMEM : GD_ECUDA;
+    std::vector<int32_t>().swap(r->rp);      // the device copy is the request's CSR now
+    std::vector<int32_t>().swap(r->ci);
+    return GD_OK;
+}
+
+void release_csr(Request *r, cudaStream_t st) {
+    if (r->d_rp) cudaFreeAsync(r->d_rp, st);
+    if (r->d_ci) cudaFreeAsync(r->d_ci, st);
+    r->d_rp = r->d_ci = nullptr;
+}
+
+void stager_main(Service *s) {
+    cudaSetDevice(s->parent->device);
+    while (true) {
+        Request *r = nullptr;
+        {
+            std::unique_lock<std::mutex> lk(s->mu);
+            s->cv_admit.wait(lk, [&] { return s->stop || (r = admit(s)) != nullptr; });
+            if (s->stop && !r) break;
+        }
+        const int rc = stage(s, r);
+        {
+            std::lock_guard<std::mutex> lk(s->mu);
+            if (rc == GD_OK) {
+                r->state = 3;
+                s->admitted.push_back(r);
+            } else {
+                release_csr(r, s->stage_stream);
+                r->status = rc;
+                r->state = 2;
+                r->t_start = r->t_end = s->now_ms();
+                s->inflight -= r->footprint;
+            }
+        }
+        if (rc == GD_OK) s->cv_work.notify_one();
+        else s->cv_done.notify_all();
+    }
+}
+
+// Work for one worker (lock held): the oldest admitted request, plus every
+// other admitted small request when it is small.
+bool pick(Service *s, std::vector<Request *> &out) {
+    out.clear();
+    if (s->admitted.empty()) return false;
+    out.push_back(s->admitted.front());
+    s->admitted.pop_front();
     if (out[0]->n <= SMALL_N) {
-        for (auto it = s->queue.begin(); it != s->queue.end() && (int32_t)out.size() < BATCH_MAX_GRAPHS;) {
-            Request *r = *it;
-            if (r->n <= SMALL_N && s->fits(r->footprint)) {
-                s->inflight += r->footprint;
-                out.push_back(r);
-                it = s->queue.erase(it);
+        for (auto it = s->admitted.begin(); it != s->admitted.end() && (int32_t)out.size() < BATCH_MAX_GRAPHS;) {
+            if ((*it)->n <= SMALL_N) {
+                out.push_back(*it);
+                it = s->admitted.erase(it);
             } else {
                 ++it;
             }
@@ -102,32 +183,41 @@ bool pick(Service *s, std::vector<Request *> &out) {
 
 void run_single(gd_ctx *ctx, Request *r) {
     gd_graph *g = nullptr;
-    int rc = gd_create_csr(ctx, r->n, r->nnz, r->rp.data(), r->ci.empty() ? r->rp.data() : r->ci.data(), 0,
-                           ctx->stream, &g);
+    int rc = gd_create_csr(ctx, r->n, r->nnz, r->d_rp, r->d_ci, GD_DEVICE_PTRS | GD_BORROW, ctx->stream, &g);
     if (rc == GD_OK) rc = gd_count_global(g, r->result);
     gd_destroy_graph(g);
     r->status = rc;
 }
 
-void run_batch(gd_ctx *ctx, std::vector<Request *> &rs) {
+// Worker buffers of the batched launch: the requests' device pointers and the
+// counts.
+struct BatchBufs {
+    const int32_t **d_ptrs = nullptr;    // [2 * BATCH_MAX_GRAPHS]
+    uint64_t *d_out = nullptr;           // [BATCH_MAX_GRAPHS * 15]
+};
+
+void run_batch(gd_ctx *ctx, BatchBufs &bb, std::vector<Request *> &rs) {
     const int32_t G = (int32_t)rs.size();
-    std::vector<int32_t> gnp((size_t)G + 1, 0);
-    int64_t N = 0, E = 0;
-    for (int32_t i = 0; i < G; i++) { N += rs[i]->n; E += rs[i]->nnz; }
-    std::vector<int32_t> rp((size_t)N + 1), ci((size_t)std::max<int64_t>(E, 1));
-    int64_t no = 0, eo = 0;
+    std::vector<const int32_t *> ptrs((size_t)2 * G);
+    std::vector<int32_t> nn((size_t)G);
+    std::vector<int64_t> ns((size_t)G);
     for (int32_t i = 0; i < G; i++) {
-        Request *r = rs[i];
-        gnp[i] = (int32_t)no;
-        for (int32_t u = 0; u < r->n; u++) rp[no + u] = (int32_t)(eo + r->rp[u]);
-        for (int64_t p = 0; p < r->nnz; p++) ci[eo + p] = (int32_t)(no + r->ci[p]);
-        no += r->n;
-        eo += r->nnz;
+        ptrs[i] = rs[i]->d_rp;
+        ptrs[G + i] = rs[i]->d_ci;
+        nn[i] = rs[i]->n;
+        ns[i] = rs[i]->nnz;
     }
-    gnp[G] = (int32_t)no;
-    rp[no] = (int32_t)eo;
     std::vector<uint64_t> out((size_t)G * 15);
-    int rc = gd_count_batch(ctx, G, gnp.data(), rp.data(), ci.data(), 0, out.data());
+    cudaError_t e = cudaMemcpyAsync(bb.d_ptrs, ptrs.data(), sizeof(const int32_t *) * ptrs.size(),
+                                    cudaMemcpyHostToDevice, ctx->stream);
+    int rc = e == cudaSuccess ? GD_OK : GD_ECUDA;
+    if (rc == GD_OK)
+        rc = gd_count_batch_gather(ctx, G, bb.d_ptrs, bb.d_ptrs + G, nn.data(), ns.data(), 0, bb.d_out);
+    if (rc == GD_OK) {
+        e = cudaMemcpyAsync(out.data(), bb.d_out, sizeof(uint64_t) * out.size(), cudaMemcpyDeviceToHost, ctx->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+        if (e != cudaSuccess) rc = GD_ECUDA;
+    }
     if (rc != GD_OK && G > 1) {
         // one bad request must not fail the others: count them one by one
         for (Request *r : rs) run_single(ctx, r);
@@ -142,6 +232,10 @@ void run_batch(gd_ctx *ctx, std::vector<Request *> &rs) {
 void worker_main(Service *s, int32_t k) {
     gd_ctx *ctx = s->sub[k];
     cudaSetDevice(ctx->device);
+    BatchBufs bb;
+    const bool bufs_ok =
+        cudaMalloc((void **)&bb.d_ptrs, sizeof(const int32_t *) * 2 * BATCH_MAX_GRAPHS) == cudaSuccess &&
+        cudaMalloc((void **)&bb.d_out, sizeof(uint64_t) * 15 * BATCH_MAX_GRAPHS) == cudaSuccess;
     std::vector<Request *> work;
     while (true) {
         {
@@ -150,15 +244,21 @@ void worker_main(Service *s, int32_t k) {
             // only what pick() hands out in this round is run
             work.clear();
             s->cv_work.wait(lk, [&] { return s->stop || pick(s, work); });
-            if (s->stop && work.empty()) break;      // stop requested and nothing picked
+            if (s->stop) {
+                for (Request *r : work) s->admitted.push_front(r);   // released at shutdown
+                break;
+            }
             const double t = s->now_ms();
             for (Request *r : work) { r->state = 1; r->t_start = t; r->slot = k; r->batched = work.size() > 1 || r->n <= SMALL_N; }
         }
         if (work.size() == 1 && work[0]->n > SMALL_N) {
             run_single(ctx, work[0]);
+        } else if (bufs_ok) {
+            run_batch(ctx, bb, work);
         } else {
-            run_batch(ctx, work);
+            for (Request *r : work) run_single(ctx, r);
         }
+        for (Request *r : work) release_csr(r, ctx->stream);
         // keep the worker's block cache within its share of the budget
         if (s->budget && ctx->pooled > s->budget / (size_t)s->slots) gd_pool_release(ctx);
         {
@@ -173,8 +273,12 @@ void worker_main(Service *s, int32_t k) {
             else s->launches_single++;
         }
         s->cv_done.notify_all();
+        s->cv_admit.notify_all();
         s->cv_work.notify_all();
     }
+    cudaStreamSynchronize(ctx->stream);
+    if (bb.d_ptrs) cudaFree(bb.d_ptrs);
+    if (bb.d_out) cudaFree(bb.d_out);
 }
 
 }  // namespace
@@ -187,7 +291,15 @@ void serve_destroy(gd_ctx *ctx) {
         s->stop = true;
     }
     s->cv_work.notify_all();
+    s->cv_admit.notify_all();
+    if (s->stager.joinable()) s->stager.join();
     for (auto &t : s->workers) t.join();
+    cudaSetDevice(ctx->device);
+    for (auto &kv : s->all) release_csr(kv.second, s->stage_stream);
+    if (s->stage_stream) {
+        cudaStreamSynchronize(s->stage_stream);
+        cudaStreamDestroy(s->stage_stream);
+    }
     for (gd_ctx *c : s->sub) gd_destroy(c);
     for (auto &kv : s->all) delete kv.second;
     delete s;
@@ -208,6 +320,17 @@ int gd_serve_start(gd_ctx *ctx, int32_t slots, size_t hbm_budget_bytes) {
     s->parent = ctx;
     s->slots = slots;
     s->budget = hbm_budget_bytes ? hbm_budget_bytes : ctx->budget;
+    if (!s->budget) {
+        // no budget given: 45% of the device memory free now, so that the
+        // admitted footprints and the workers' block caches (each kept
+        // within budget / slots) stay below what the device has
+        size_t free_b = 0, total_b = 0;
+        if (cudaSetDevice(ctx->device) != cudaSuccess || cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+            delete s;
+            return GD_ECUDA;
+        }
+        s->budget = free_b / 20 * 9;
+    }
     s->t0 = std::chrono::steady_clock::now();
     for (int32_t k = 0; k < slots; k++) {
         gd_ctx *c = nullptr;
@@ -219,7 +342,14 @@ int gd_serve_start(gd_ctx *ctx, int32_t slots, size_t hbm_budget_bytes) {
         }
         s->sub.push_back(c);
     }
+    if (cudaSetDevice(ctx->device) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&s->stage_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        for (gd_ctx *x : s->sub) gd_destroy(x);
+        delete s;
+        return GD_ECUDA;
+    }
     ctx->service = s;
+    s->stager = std::thread(stager_main, s);
     for (int32_t k = 0; k < slots; k++) s->workers.emplace_back(worker_main, s, k);
     return GD_OK;
 }
@@ -256,7 +386,7 @@ int gd_submit(gd_ctx *ctx, const gd_request_desc *desc, gd_req *id) {
         s->queue.push_back(r);
         *id = r->id;
     }
-    s->cv_work.notify_one();
+    s->cv_admit.notify_one();
     return GD_OK;
 }
 
@@ -303,7 +433,7 @@ int gd_serve_stats(gd_ctx *ctx, int64_t *queued, int64_t *running, size_t *infli
     std::lock_guard<std::mutex> lk(s->mu);
     int64_t run = 0;
     for (auto &kv : s->all) run += kv.second->state == 1;
-    if (queued) *queued = (int64_t)s->queue.size();
+    if (queued) *queued = (int64_t)(s->queue.size() + s->admitted.size());
     if (running) *running = run;
     if (inflight_bytes) *inflight_bytes = s->inflight;
     if (batched_launches) *batched_launches = s->launches_batched;

@@ -67,7 +67,7 @@ class gd_options(ctypes.Structure):
     _fields_ = [("variant", ctypes.c_int32), ("block_threads", ctypes.c_int32),
                 ("ctas_per_sm", ctypes.c_int32), ("smem_table_max", ctypes.c_int32),
                 ("bitmap_max_outdeg", ctypes.c_int32), ("hub_wedges_log2", ctypes.c_int32),
-                ("hub_pull", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
+                ("hub_pull", ctypes.c_int32), ("batch_threads", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
 
 
 class gd_tune_result(ctypes.Structure):
@@ -102,6 +102,7 @@ def load():
             "gd_count_global": (ctypes.c_int, [vp, vp]),
             "gd_count_per_edge": (ctypes.c_int, [vp, vp, ctypes.c_int, vp]),
             "gd_count_batch": (ctypes.c_int, [vp, i32, vp, vp, vp, ctypes.c_int, vp]),
+            "gd_count_batch_gather": (ctypes.c_int, [vp, i32, vp, vp, vp, vp, ctypes.c_int, vp]),
             "gd_profile_begin": (ctypes.c_int, [vp]),
             "gd_profile_end": (ctypes.c_int, [vp, vp, i32, ctypes.POINTER(i32)]),
             "gd_kernel_launches": (i64, [vp]),
@@ -115,6 +116,7 @@ def load():
             "gd_serve_stop": (ctypes.c_int, [vp]),
             "gd_footprint_estimate": (ctypes.c_int, [vp, i32, i64, ctypes.c_int, ctypes.POINTER(sz)]),
             "gd_autotune": (ctypes.c_int, [vp, ctypes.c_int, i32, vp]),
+            "gd_autotune_batch": (ctypes.c_int, [vp, i32, vp, vp, vp, ctypes.c_int, vp, vp]),
             "gd_set_options": (ctypes.c_int, [vp, vp]),
             "gd_get_options": (ctypes.c_int, [vp, vp]),
             "gd_topk": (ctypes.c_int, [vp, vp, i64, i64, ctypes.c_int, i64, vp, vp, vp]),
@@ -217,6 +219,14 @@ def gd_count_batch(ctx, num_graphs: int, graph_node_ptr: int, row_ptr: int, col_
            "gd_count_batch")
 
 
+def gd_count_batch_gather(ctx, num_graphs: int, row_ptrs: int, col_idxs: int, num_nodes: int, num_slots: int,
+                          flags: int, out_ptr: int) -> None:
+    """row_ptrs / col_idxs: device arrays of device pointers; num_nodes
+    (int32) / num_slots (int64): host arrays; out: device."""
+    _check(ctx, load().gd_count_batch_gather(ctx, num_graphs, row_ptrs, col_idxs, num_nodes, num_slots, flags,
+                                             out_ptr), "gd_count_batch_gather")
+
+
 def gd_profile_begin(ctx) -> None:
     _check(ctx, load().gd_profile_begin(ctx), "gd_profile_begin")
 
@@ -288,6 +298,15 @@ def gd_gfd_batch(ctx, num_graphs: int, graph_node_ptr: int, row_ptr: int, counts
                  stream: int = 0) -> None:
     _check(ctx, load().gd_gfd_batch(ctx, num_graphs, graph_node_ptr, row_ptr, counts, GD_DEVICE_PTRS, out,
                                     stream or None), "gd_gfd_batch")
+
+
+def gd_autotune_batch(ctx, num_graphs: int, graph_node_ptr: int, row_ptr: int, col_idx: int, flags: int,
+                      out_ptr: int) -> dict:
+    r = gd_tune_result()
+    _check(ctx, load().gd_autotune_batch(ctx, num_graphs, graph_node_ptr, row_ptr, col_idx, flags, out_ptr,
+                                         ctypes.byref(r)), "gd_autotune_batch")
+    return {"batch_threads": r.best.batch_threads, "best_ms": r.best_ms, "default_ms": r.default_ms,
+            "trials": r.trials}
 
 
 def gd_autotune(ctx, graph, per_edge: bool = False, max_trials: int = 24) -> dict:
@@ -514,6 +533,38 @@ class Context:
         if capture:
             flags |= GD_CAPTURE
         gd_count_batch(self.handle, G, pg, pr, pc, flags, po)
+        return out[:G]
+
+    def autotune_batch(self, batch, out=None) -> dict:
+        """gd_autotune_batch on a packed batch (the batch_threads option)."""
+        gnp, rp, ci = batch.graph_node_ptr, batch.row_ptr, batch.col_idx
+        G = int(gnp.shape[0]) - 1
+        pg, dev = _ptr(gnp)
+        pr, _ = _ptr(rp)
+        pc, _ = _ptr(ci if ci.shape[0] > 0 else (np.zeros(1, np.int32) if not dev else ci))
+        if out is None:
+            out = np.zeros((max(G, 1), 15), dtype=np.uint64)
+        po, odev = _ptr(out)
+        flags = (GD_DEVICE_PTRS if dev else 0) | (GD_OUT_DEVICE if odev else 0)
+        return gd_autotune_batch(self.handle, G, pg, pr, pc, flags, po)
+
+    def count_batch_gather(self, graphs, out=None, capture: bool = False):
+        """Per-graph global counts of graphs held as separate device CSRs:
+        `graphs` is a list of (row_ptr, col_idx) torch int32 CUDA tensors.
+        Returns a torch int64 tensor [G, 15] (uint64 bit patterns)."""
+        import torch
+        G = len(graphs)
+        dev = graphs[0][0].device if G else torch.device("cuda")
+        rps = torch.tensor([r.data_ptr() for r, _ in graphs], dtype=torch.int64, device=dev)
+        cis = torch.tensor([c.data_ptr() for _, c in graphs], dtype=torch.int64, device=dev)
+        nn = np.array([r.shape[0] - 1 for r, _ in graphs], dtype=np.int32)
+        ns = np.array([c.shape[0] for _, c in graphs], dtype=np.int64)
+        if out is None:
+            out = torch.empty((max(G, 1), 15), dtype=torch.int64, device=dev)
+        torch.cuda.synchronize()
+        gd_count_batch_gather(self.handle, G, rps.data_ptr(), cis.data_ptr(), nn.ctypes.data, ns.ctypes.data,
+                              GD_CAPTURE if capture else 0, out.data_ptr())
+        self._keep = (rps, cis)
         return out[:G]
 
 

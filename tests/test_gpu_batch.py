@@ -100,3 +100,77 @@ def test_batch_captured_graph_replays(ctx):
     ctx.count_batch(db2, out=out2, capture=True)
     torch.cuda.synchronize()
     assert np.array_equal(out2.cpu().numpy().view(np.uint64), np.array(ctx.count_batch(b2)))
+
+
+def _device_graphs(torch, graphs):
+    return [(torch.from_numpy(g.row_ptr).cuda(),
+             torch.from_numpy(g.col_idx if g.nnz else np.zeros(0, np.int32)).cuda()) for g in graphs]
+
+
+@pytest.mark.parametrize("capture", [False, True])
+def test_batch_gather_from_separate_device_csrs(ctx, capture):
+    """gd_count_batch_gather: graphs that sit in device memory one by one are
+    packed on the device by one gather kernel and counted in the batched
+    launch; with GD_CAPTURE the gather, validation and count replay as one
+    captured CUDA graph, and a change of graphs re-captures."""
+    torch = pytest.importorskip("torch")
+    gs = [inputs.batch_graph(i, seed=31) for i in range(120)]
+    gs += [inputs.from_edges(0, []), inputs.from_edges(3, [(0, 1)]),
+           inputs.from_edges(30, [(i, j) for i in range(30) for j in range(i + 1, 30)])]
+    if not capture:
+        gs.append(inputs.erdos_renyi(1100, 0.01, 6))      # above the shared-memory limit
+    dg = _device_graphs(torch, gs)
+    want = expected(gs)
+    for _ in range(3 if capture else 1):
+        got = ctx.count_batch_gather(dg, capture=capture)
+        torch.cuda.synchronize()
+        got = got.cpu().numpy().view(np.uint64)
+        for i in range(len(gs)):
+            assert [int(x) for x in got[i]] == list(want[i]), (i, gs[i].name)
+    gs2 = [inputs.batch_graph(i, seed=32) for i in range(123)]
+    got2 = ctx.count_batch_gather(_device_graphs(torch, gs2), capture=capture)
+    torch.cuda.synchronize()
+    want2 = expected(gs2)
+    got2 = got2.cpu().numpy().view(np.uint64)
+    for i in range(len(gs2)):
+        assert [int(x) for x in got2[i]] == list(want2[i])
+
+
+def test_batch_gather_rejects_bad_row_ptr(ctx):
+    torch = pytest.importorskip("torch")
+    g = inputs.erdos_renyi(40, 0.2, 3)
+    rp = g.row_ptr.copy()
+    rp[0] = 1
+    dg = [(torch.from_numpy(rp).cuda(), torch.from_numpy(g.col_idx).cuda())]
+    with pytest.raises(gd.GDError) as ei:
+        ctx.count_batch_gather(dg)
+    assert ei.value.code == gd.GD_EINVAL
+    # the context stays usable
+    got = ctx.count_batch_gather(_device_graphs(torch, [g]))
+    torch.cuda.synchronize()
+    assert [int(x) for x in got.cpu().numpy().view(np.uint64)[0]] == list(expected([g])[0])
+
+
+def test_batch_autotune_keeps_counts_and_caches(tmp_path):
+    """gd_autotune_batch times the batched kernel's CTA sizes on a batch and
+    keeps the fastest; the counts are the same under every choice, and the
+    choice is cached by the batch's size signature."""
+    from paper_1506_04322_gb300 import autotune
+    gs = [inputs.batch_graph(i, seed=41) for i in range(300)] + [inputs.erdos_renyi(900, 0.01, 2)]
+    b = inputs.pack(gs)
+    want = expected(gs)
+    with gd.Context(0) as c:
+        cache = str(tmp_path / "tune.json")
+        r = autotune.tuned_batch_options(c, b, cache_path=cache)
+        assert not r["cached"] and r["trials"] >= 3 and r["best_ms"] <= r["default_ms"]
+        assert c.options().batch_threads == r["options"]["batch_threads"]
+        got = np.array(c.count_batch(b))
+        for i in range(len(gs)):
+            assert [int(x) for x in got[i]] == list(want[i])
+        r2 = autotune.tuned_batch_options(c, b, cache_path=cache)
+        assert r2["cached"] and r2["options"] == r["options"]
+        for t in (128, 256, 512, 1024):
+            o = c.options()
+            o.batch_threads = t
+            c.set_options(o)
+            assert np.array_equal(np.array(c.count_batch(b)), got)

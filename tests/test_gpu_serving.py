@@ -116,3 +116,30 @@ def test_bad_request_fails_alone():
             with gd.Context(0) as alone, alone.graph(x) as h:
                 assert counts == h.count_global()
         ctx.serve_stop()
+
+
+def test_large_request_is_not_starved():
+    """A large request queued among many small ones, under a budget that it
+    fits only while no small request is admitted: once it has been passed
+    over for GD_SERVE_MAX_BYPASS_MS, admissions stop until it fits, so it
+    finishes long before the small requests queued after it."""
+    small = [inputs.chung_lu(4000, 2.3, 16000, 0.0, 5100 + k) for k in range(400)]
+    large = inputs.chung_lu(60000, 2.1, 480000, 0.0, 5099)
+    with gd.Context(0) as probe:
+        fp_s = max(probe.footprint_estimate(g.n, g.nnz) for g in small)
+        fp_l = probe.footprint_estimate(large.n, large.nnz)
+    with gd.Context(0) as ctx:
+        ctx.serve_start(slots=4, hbm_budget_bytes=fp_l + fp_s // 2)
+        ids = [ctx.submit(g) for g in small[:20]]
+        lid = ctx.submit(large)
+        later = [ctx.submit(g) for g in small[20:]]
+        res = collect(ctx, ids + [lid] + later)
+        rc, counts, st = res[lid]
+        assert rc == gd.GD_OK
+        with gd.Context(0) as alone, alone.graph(large) as h:
+            assert counts == h.count_global()
+        before = sum(1 for r in later if res[r][2]["start_ms"] < st["start_ms"])
+        assert before < len(later) // 2, f"{before} later requests started before the large one"
+        assert st["end_ms"] - st["submit_ms"] < 2000
+        assert all(res[r][0] == gd.GD_OK for r in ids + later)
+        ctx.serve_stop()
