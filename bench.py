@@ -64,9 +64,10 @@ def parse():
     ap.add_argument("--serving-requests", type=int, default=1000, help="requests of the serving trace")
     ap.add_argument("--cpu-o2", action="store_true",
                     help="also time the O2 oracle on the whole graph with every host core (minutes)")
-    ap.add_argument("--workload", default="chung_lu_1m", choices=["chung_lu_1m", "chung_lu_400k", "rmat_22"],
+    ap.add_argument("--workload", default="chung_lu_1m", choices=["chung_lu_1m", "chung_lu_400k", "rmat_22", "rmat_20"],
                     help="chung_lu_400k: a 4M-edge graph of the same family, for profiler captures; "
-                         "rmat_22: the R-MAT scale-22 graph (use with --global-only)")
+                         "rmat_22: the R-MAT scale-22 graph (use with --global-only); rmat_20: R-MAT scale 20, "
+                         "edge factor 16, for profiler captures of the global-count kernels")
     return ap.parse_args()
 
 
@@ -811,6 +812,9 @@ def run_gd(args):
         g.name = "chung_lu_n400k_gamma2.1_cap20k"
     elif args.workload == "rmat_22":
         g = inputs.rmat_22()           # the global counts (per-edge output would be 7.7 GB)
+    elif args.workload == "rmat_20":
+        g = inputs.rmat(20, 16 << 20, 0.57, 0.19, 0.19, 3)
+        g.name = "rmat_scale20_ef16"
     else:
         g = inputs.chung_lu_1m()
 
@@ -873,7 +877,7 @@ def run_gd(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
         "config": {"workload": g.name, "n": g.n, "m": g.m,
                    "mode": "global" if args.global_only else "per-edge (15 columns) + global",
-                   "variant": "oriented", "seed": {"chung_lu_1m": 2, "chung_lu_400k": 9, "rmat_22": 3}[args.workload],
+                   "variant": "oriented", "seed": {"chung_lu_1m": 2, "chung_lu_400k": 9, "rmat_22": 3, "rmat_20": 3}[args.workload],
                    "l2": "flushed between timed steps (512 MB write)",
                    "parallelism": f"replicas x{ws}"},
         "e2e": rec["e2e"],

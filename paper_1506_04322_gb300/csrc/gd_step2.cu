@@ -1420,10 +1420,13 @@ __global__ void k_pull_mark(CycleArgs a, int32_t h0, int32_t nb, unsigned long l
     }
 }
 
-template <int L>
+// add a mask into the lowest LA planes (the caller guarantees that no
+// counter passes 2^LA - 1 on the way)
+template <int LA, int L>
 __device__ __forceinline__ void plane_add(unsigned long long (&P)[L], unsigned long long x) {
+    static_assert(LA <= L, "active planes");
 #pragma unroll
-    for (int b = 0; b < L; b++) {
+    for (int b = 0; b < LA; b++) {
         const unsigned long long c = P[b] & x;
         P[b] ^= x;
         x = c;
@@ -1482,12 +1485,12 @@ k_pull_thread(CycleArgs a, int32_t h0, int32_t nb, const unsigned long long *__r
             const int32_t v0 = __ldg(a.ci + p), v1 = __ldg(a.ci + p + 1);
             const int32_t v2 = __ldg(a.ci + p + 2), v3 = __ldg(a.ci + p + 3);
             const unsigned long long m0 = mask[v0], m1 = mask[v1], m2 = mask[v2], m3 = mask[v3];
-            plane_add<PULL_TPLANES>(P, m0);
-            plane_add<PULL_TPLANES>(P, m1);
-            plane_add<PULL_TPLANES>(P, m2);
-            plane_add<PULL_TPLANES>(P, m3);
+            plane_add<PULL_TPLANES, PULL_TPLANES>(P, m0);
+            plane_add<PULL_TPLANES, PULL_TPLANES>(P, m1);
+            plane_add<PULL_TPLANES, PULL_TPLANES>(P, m2);
+            plane_add<PULL_TPLANES, PULL_TPLANES>(P, m3);
         }
-        for (; p < e; p++) plane_add<PULL_TPLANES>(P, mask[__ldg(a.ci + p)]);
+        for (; p < e; p++) plane_add<PULL_TPLANES, PULL_TPLANES>(P, mask[__ldg(a.ci + p)]);
         unsigned long long any = 0;
 #pragma unroll
         for (int i = 1; i < PULL_TPLANES; i++) any |= P[i];
@@ -1506,6 +1509,7 @@ k_pull_thread(CycleArgs a, int32_t h0, int32_t nb, const unsigned long long *__r
 // 64 counters of its own, summed by k_pull_heavy after all chunks.
 constexpr int PULL_CHUNK = 1024;
 constexpr int PULL_CPLANES = 11;      // a chunk's counters are <= 1024
+constexpr int PULL_LPLANES = 6;       // a lane's share of a chunk: <= 32 masks
 
 struct PullItem { int32_t y, chunk, heavy; };
 
@@ -1541,18 +1545,25 @@ k_pull_warp(CycleArgs a, int32_t h0, int32_t nb, const unsigned long long *__res
             const int32_t v0 = __ldg(a.ci + p), v1 = __ldg(a.ci + p + WARP);
             const int32_t v2 = __ldg(a.ci + p + 2 * WARP), v3 = __ldg(a.ci + p + 3 * WARP);
             const unsigned long long m0 = mask[v0], m1 = mask[v1], m2 = mask[v2], m3 = mask[v3];
-            plane_add<PULL_CPLANES>(P, m0);
-            plane_add<PULL_CPLANES>(P, m1);
-            plane_add<PULL_CPLANES>(P, m2);
-            plane_add<PULL_CPLANES>(P, m3);
+            plane_add<PULL_LPLANES, PULL_CPLANES>(P, m0);
+            plane_add<PULL_LPLANES, PULL_CPLANES>(P, m1);
+            plane_add<PULL_LPLANES, PULL_CPLANES>(P, m2);
+            plane_add<PULL_LPLANES, PULL_CPLANES>(P, m3);
         }
-        for (; p < e; p += WARP) plane_add<PULL_CPLANES>(P, mask[__ldg(a.ci + p)]);
-        // butterfly: every lane ends with the chunk's total (<= 1024 each)
+        for (; p < e; p += WARP) plane_add<PULL_LPLANES, PULL_CPLANES>(P, mask[__ldg(a.ci + p)]);
+        unsigned long long any = 0;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
+        for (int i = 0; i < PULL_LPLANES; i++) any |= P[i];
+        if (!__any_sync(FULL, any != 0)) continue;      // no neighbour below a batch hub
+        // butterfly: every lane ends with the chunk's total (<= 1024 each);
+        // after level l the counters need PULL_LPLANES + l + 1 planes
+#pragma unroll
+        for (int l = 0; l < 5; l++) {
+            const int o = 16 >> l;
             unsigned long long c = 0;
 #pragma unroll
             for (int i = 0; i < PULL_CPLANES; i++) {
+                if (i > PULL_LPLANES + l) break;
                 const unsigned long long q = __shfl_xor_sync(FULL, P[i], o);
                 const unsigned long long s = P[i] ^ q ^ c;
                 c = (P[i] & q) | (c & (P[i] ^ q));
