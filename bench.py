@@ -56,6 +56,7 @@ def parse():
     ap.add_argument("--bitmap-max", type=int, default=None, help="gd_options.bitmap_max_outdeg")
     ap.add_argument("--hub-log2", type=int, default=None, help="gd_options.hub_wedges_log2")
     ap.add_argument("--hub-pull", type=int, default=None, help="gd_options.hub_pull (0 auto, 1 never, 2 always)")
+    ap.add_argument("--medium-cl", type=int, default=None, help="gd_options.medium_cluster_log2 (above 40: never)")
     ap.add_argument("--global-only", action="store_true", help="time gd_count_global instead")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-graphs measurement")
     ap.add_argument("--no-serving", action="store_true", help="skip the request-loop measurement")
@@ -819,7 +820,8 @@ def run_gd(args):
         g = inputs.chung_lu_1m()
 
     ctx = gd.Context(device, smem_table_max=args.smem_table, bitmap_max_outdeg=args.bitmap_max,
-                     hub_wedges_log2=args.hub_log2, hub_pull=args.hub_pull)
+                     hub_wedges_log2=args.hub_log2, hub_pull=args.hub_pull,
+                     medium_cluster_log2=args.medium_cl)
     rec, h, out = measure_workload(gd, torch, ctx, g, device, args.global_only, args.steps, args.warmup,
                                    ws, rank, args.hub_log2 or 17)
 

@@ -131,7 +131,10 @@ typedef struct gd_options {
                                  nodes, 512 up to 1024; else 128, 256 or 512 for
                                  the 512-node kernel and 256, 512 or 1024 for
                                  the 1024-node kernel (the nearest is taken)  */
-    int32_t reserved[4];
+    int32_t medium_cluster_log2;  /* medium-tier vertices with at least 2^k wedges
+                                     are counted by clusters of 8 CTAs sharing one
+                                     table (0: default 16; above 40: never)      */
+    int32_t reserved[3];
 } gd_options;
 
 enum { GD_PULL_AUTO = 0, GD_PULL_NEVER = 1, GD_PULL_ALWAYS = 2 };
@@ -266,7 +269,8 @@ typedef struct gd_tune_result {
 
 /* Time counts of g (per_edge != 0: gd_count_per_edge, else gd_count_global)
  * under up to max_trials option sets -- shared-memory wedge table size,
- * bitmap out-degree limit, hub wedge threshold -- with CUDA events on the
+ * bitmap out-degree limit, hub wedge threshold, then the medium tier's
+ * cluster cut-over -- with CUDA events on the
  * graph's stream, and make the fastest the context's options.  The counts
  * are identical under every option set; only the time differs. */
 int gd_autotune(gd_graph *g, int per_edge, int32_t max_trials, gd_tune_result *res);

@@ -57,7 +57,8 @@ def tuned_options(ctx: "gd.Context", graph_handle: "gd.Graph", g, per_edge: bool
         ctx.set_options(o)
         return dict(cache[key], cached=True)
     res = graph_handle.autotune(per_edge=per_edge, max_trials=max_trials)
-    entry = {"options": {k: res[k] for k in ("smem_table_max", "bitmap_max_outdeg", "hub_wedges_log2")},
+    entry = {"options": {k: res[k] for k in ("smem_table_max", "bitmap_max_outdeg", "hub_wedges_log2",
+                                             "medium_cluster_log2")},
              "best_ms": res["best_ms"], "default_ms": res["default_ms"], "trials": res["trials"]}
     if path:
         cache[key] = entry

@@ -514,6 +514,7 @@ static int check_options(gd_options *o) {
         o->hub_wedges_log2 > 40) return GD_EINVAL;
     if (o->hub_pull < GD_PULL_AUTO || o->hub_pull > GD_PULL_ALWAYS) return GD_EINVAL;
     if (o->batch_threads < 0 || o->batch_threads > 1024) return GD_EINVAL;
+    if (o->medium_cluster_log2 < 0 || o->medium_cluster_log2 > 64) return GD_EINVAL;
     return GD_OK;
 }
 
@@ -1140,6 +1141,17 @@ int gd_autotune(gd_graph *g, int per_edge, int32_t max_trials, gd_tune_result *r
                 trials++;
                 if (ms < best_ms) { best_ms = ms; best = o; }
             }
+    // the medium tier's cluster cut-over, on the best set so far
+    for (int32_t mc : {15, 17, 41}) {
+        if (trials >= max_trials) break;
+        gd_options o = best;
+        o.medium_cluster_log2 = mc;
+        ctx->opt = o;
+        double ms = 0;
+        if ((rc = time_once(&ms))) { ctx->opt = start; cudaEventDestroy(e0); cudaEventDestroy(e1); return rc; }
+        trials++;
+        if (ms < best_ms) { best_ms = ms; best = o; }
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     ctx->opt = best;

@@ -44,6 +44,7 @@ enum CounterIdx {
     C_CL0 = 4,      // 4 clique buckets by out-degree: <=CL_D0, <=CL_D1, <=CL_D2, larger
     C_DYN = 8,      // dynamic work index of the medium tier
     C_TINY = 9,     // vertices in the warp-level wedge tier
+    C_DYN2 = 11,    // dynamic work index of the medium tier's cluster kernel
     C_MB0 = 16,     // medium tier: vertices per log2(wedges) bucket (40 buckets)
     C_MOFF = 64,    // medium tier: placement offsets per bucket (40)
     C_CLD0 = 104,   // clique kernels: work counters (pass x bucket, 8)

@@ -45,6 +45,7 @@
 //            GPU taking an equal share of the batch's wedges, dense tables of
 //            n counters (a few at a time, so they stay in L2).
 #include <cuda_runtime.h>
+#include <cooperative_groups.h>
 
 #include <algorithm>
 #include <vector>
@@ -1178,6 +1179,100 @@ k_cycles_medium(CycleArgs a) {
     }
 }
 
+// Medium tier, vertices of at least 2^MED_CL_LOG2 wedges: a cluster of MCL
+// CTAs takes one vertex at a time and shares one open-addressing table in
+// global memory, so that only one table per cluster is live (a few tens of
+// MB for the whole GPU, which stay in L2, where one table per CTA did not).
+// The vertex's wedges are split evenly over all warps of the cluster; the
+// cluster's hardware barrier separates counting, crediting and the reset
+// (each CTA resets its share of the table).  The next vertex's index is
+// fetched by CTA 0 and read by the others from its shared memory.
+constexpr int MCL = 8;
+constexpr int MED_CL_LOG2 = 16;
+
+template <bool CREDIT>
+__global__ void __cluster_dims__(MCL, 1, 1) __launch_bounds__(1024, 2)
+k_cycles_medium_cl(CycleArgs a, int32_t nv_big) {
+    constexpr int THREADS = 1024, NW = THREADS / 32;
+    namespace cg = cooperative_groups;
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = (int)cl.block_rank();
+    __shared__ unsigned long long item[NW][WARP];
+    __shared__ long long wsum[NW];
+    __shared__ int32_t next[2];
+    extern __shared__ long long pre[];          // MED_PCAP + 1 entries
+    const int lane = lane_id(), warp = threadIdx.x >> 5;
+    unsigned long long *tab = a.mtab + (int64_t)(blockIdx.x / MCL) * a.mcap;
+    if (rank == 0 && threadIdx.x == 0) next[0] = atomicAdd(a.counters + C_DYN2, 1);
+    item[warp][lane] = 0;
+    unsigned long long c4 = 0;
+    bool full = false;
+    const int gw = rank * NW + warp;            // warp index within the cluster
+    constexpr int GW = MCL * NW;
+    cl.sync();
+    for (int it = 0;; it++) {
+        const int32_t idx = *cl.map_shared_rank(&next[it & 1], 0);
+        if (idx >= nv_big) break;
+        const int32_t u = a.mlist[idx];
+        const int32_t bu = a.rp[u], du = a.rp[u + 1] - bu;
+        uint32_t cap = 1024;
+        while ((int64_t)cap < 2 * a.west[u] && (int64_t)cap < a.mcap) cap <<= 1;
+        const uint32_t mask = cap - 1;
+        auto count = [&](int k, int32_t q, int32_t y, bool ok, bool live) {
+            if (!ok) return;
+            const uint32_t old = mh_add(tab, mask, y);
+            if (old == 0xffffffffu) full = true;
+            else if (!CREDIT) c4 += old;
+        };
+        auto credit = [&](int k, int32_t q, int32_t y, bool ok, bool live) {
+            const uint32_t c = ok ? mh_get(tab, mask, y) : 0;
+            if (c > 1) atomicAdd(a.yacc + q, (unsigned long long)(c - 1));
+            item_add(item[warp], k, c > 1 ? c - 1 : 0, live);
+        };
+        if (du <= MED_PCAP) {
+            const long long W = wedge_prefix<THREADS>(a, u, bu, du, pre, wsum);
+            const long long w_lo = W * gw / GW, w_hi = W * (gw + 1) / GW;
+            walk_range(a, u, bu, du, pre, w_lo, w_hi, count, [&](int32_t) {});
+            cl.sync();
+            if (CREDIT) {
+                walk_range(a, u, bu, du, pre, w_lo, w_hi, credit, [&](int32_t j) {
+                    __syncwarp();
+                    const unsigned long long sv = item[warp][lane];
+                    if (sv) { atomicAdd(a.yacc + bu + j, sv); item[warp][lane] = 0; }
+                    __syncwarp();
+                });
+                cl.sync();
+            }
+        } else {
+            warp_wedges(u, du, bu, gw * WARP, du, GW * WARP, a.rp, a.ci, a.nd, count, [&](int32_t) {});
+            cl.sync();
+            if (CREDIT) {
+                warp_wedges(u, du, bu, gw * WARP, du, GW * WARP, a.rp, a.ci, a.nd, credit,
+                    [&](int32_t i0) {
+                        __syncwarp();
+                        const unsigned long long sv = item[warp][lane];
+                        if (sv) { atomicAdd(a.yacc + bu + i0 + lane, sv); item[warp][lane] = 0; }
+                        __syncwarp();
+                    });
+                cl.sync();
+            }
+        }
+        if (rank == 0 && threadIdx.x == 0) next[(it + 1) & 1] = atomicAdd(a.counters + C_DYN2, 1);
+        ulonglong2 *t2 = reinterpret_cast<ulonglong2 *>(tab);
+        const uint32_t h0 = (cap / 2) * rank / MCL, h1 = (cap / 2) * (rank + 1) / MCL;
+        for (uint32_t i = h0 + threadIdx.x; i < h1; i += THREADS) t2[i] = make_ulonglong2(MH_EMPTY, MH_EMPTY);
+        cl.sync();
+    }
+    // CTA 0's shared memory was read by the others: no CTA leaves before all
+    // have read the last index
+    cl.sync();
+    if (full) atomicOr(a.status, ERR_CAPACITY);
+    if (!CREDIT) {
+        c4 = warp_sum(c4);
+        if (lane == 0) add_u128(a.sums + 2 * (S_NUM + X_C4), 4 * c4);
+    }
+}
+
 // Hub tier preparation, once for all hubs: hoff = exclusive prefix of the
 // hubs' degrees (the hubs' rows concatenated form one flat list), hlen[j] =
 // wedges of flat neighbour j (d_v if v ranks below its hub, else 0), and
@@ -1985,17 +2080,38 @@ cudaError_t run_cycles(gd_graph *g, bool per_edge, const int32_t *cnt) {
         if (per_edge) GD_LAUNCH(g, "k_cycles_hub_clear", k_cycles_hub_clear<true>, (unsigned)(sms * 4), 256, 0, a);
         else GD_LAUNCH(g, "k_cycles_hub_clear", k_cycles_hub_clear<false>, (unsigned)(sms * 4), 256, 0, a);
     }
-    // medium tier
+    // medium tier: the largest vertices on clusters sharing one table, the
+    // rest one CTA (and table) per vertex
     if (cnt[C_MEDIUM] > 0) {
         const int32_t slots = w.mtab_ctas;    // two 1024-thread CTAs fit on an SM
-        const unsigned grid = (unsigned)(cnt[C_MEDIUM] < slots ? cnt[C_MEDIUM] : slots);
         const size_t smem = sizeof(long long) * (MED_PCAP + 1);
+        int32_t nbig = 0;
+        const int cl_log2 = g->ctx->opt.medium_cluster_log2 ? g->ctx->opt.medium_cluster_log2 : MED_CL_LOG2;
+        for (int b = cl_log2; b < MB_BUCKETS; b++) nbig += cnt[C_MB0 + b];
+        const int32_t ncl = std::min<int32_t>(std::min<int32_t>(slots, 2 * sms / MCL), nbig);
+        if (ncl < 1) nbig = 0;
+        const int32_t zero = 0;
+        if ((e = cudaMemcpyAsync(w.counters + C_DYN2, &zero, sizeof(int32_t), cudaMemcpyHostToDevice, g->stream))) return e;
+        if ((e = cudaMemcpyAsync(w.counters + C_DYN, &nbig, sizeof(int32_t), cudaMemcpyHostToDevice, g->stream))) return e;
+        if (nbig > 0) {
+            if (per_edge) {
+                if ((e = allow_smem(k_cycles_medium_cl<true>, smem))) return e;
+                GD_LAUNCH(g, "k_cycles_medium", k_cycles_medium_cl<true>, (unsigned)(ncl * MCL), 1024, smem, a, nbig);
+            } else {
+                if ((e = allow_smem(k_cycles_medium_cl<false>, smem))) return e;
+                GD_LAUNCH(g, "k_cycles_medium", k_cycles_medium_cl<false>, (unsigned)(ncl * MCL), 1024, smem, a, nbig);
+            }
+        }
+        const int32_t rest = cnt[C_MEDIUM] - nbig;
+        const unsigned grid = (unsigned)(rest < slots ? rest : slots);
+        if (rest > 0) {
         if (per_edge) {
             if ((e = allow_smem(k_cycles_medium<1024, true>, smem))) return e;
             GD_LAUNCH(g, "k_cycles_medium", (k_cycles_medium<1024, true>), grid, 1024, smem, a);
         } else {
             if ((e = allow_smem(k_cycles_medium<1024, false>, smem))) return e;
             GD_LAUNCH(g, "k_cycles_medium", (k_cycles_medium<1024, false>), grid, 1024, smem, a);
+        }
         }
     }
     // tiny tier

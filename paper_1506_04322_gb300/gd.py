@@ -67,7 +67,8 @@ class gd_options(ctypes.Structure):
     _fields_ = [("variant", ctypes.c_int32), ("block_threads", ctypes.c_int32),
                 ("ctas_per_sm", ctypes.c_int32), ("smem_table_max", ctypes.c_int32),
                 ("bitmap_max_outdeg", ctypes.c_int32), ("hub_wedges_log2", ctypes.c_int32),
-                ("hub_pull", ctypes.c_int32), ("batch_threads", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
+                ("hub_pull", ctypes.c_int32), ("batch_threads", ctypes.c_int32),
+                ("medium_cluster_log2", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
 
 
 class gd_tune_result(ctypes.Structure):
@@ -314,7 +315,8 @@ def gd_autotune(ctx, graph, per_edge: bool = False, max_trials: int = 24) -> dic
     _check(ctx, load().gd_autotune(graph, int(per_edge), max_trials, ctypes.byref(r)), "gd_autotune")
     b = r.best
     return {"smem_table_max": b.smem_table_max, "bitmap_max_outdeg": b.bitmap_max_outdeg,
-            "hub_wedges_log2": b.hub_wedges_log2, "best_ms": r.best_ms, "default_ms": r.default_ms,
+            "hub_wedges_log2": b.hub_wedges_log2, "medium_cluster_log2": b.medium_cluster_log2,
+            "best_ms": r.best_ms, "default_ms": r.default_ms,
             "trials": r.trials}
 
 
@@ -397,9 +399,12 @@ class Context:
 
     def __init__(self, device: int = 0, hbm_budget_bytes: int = 0, variant: int = GD_VARIANT_AUTO,
                  smem_table_max: int | None = None, bitmap_max_outdeg: int | None = None,
-                 hub_wedges_log2: int | None = None, hub_pull: int | None = None):
+                 hub_wedges_log2: int | None = None, hub_pull: int | None = None,
+                 medium_cluster_log2: int | None = None):
         o = gd_default_options()
         o.variant = variant
+        if medium_cluster_log2 is not None:
+            o.medium_cluster_log2 = medium_cluster_log2
         if hub_pull is not None:
             o.hub_pull = hub_pull
         if smem_table_max:
