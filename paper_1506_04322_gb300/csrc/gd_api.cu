@@ -258,7 +258,7 @@ size_t estimate_footprint(gd_ctx *ctx, int64_t n, int64_t nnz, bool per_edge, bo
         b += round_block((size_t)std::min<int64_t>(8 * cap * ctas, std::max<int64_t>(8 * cap, medium_table_limit(nnz))));
     }
     if (per_edge) b += round_block(sizeof(unsigned long long) * 2 * (size_t)nnz);   // triangle records (typical)
-    if (!per_edge && n > 0) {
+    if (n > 0) {
         // pull form of the hub tier: node masks, chunks, heavy-node counters
         const size_t items = (size_t)(nnz / 64 + nnz / 1024 + 1), heavy = (size_t)(nnz / 1024 + 1);
         b += round_block(8 * (size_t)n) + round_block(12 * items) + round_block(4 * heavy) +
@@ -357,9 +357,9 @@ int ensure_hub_scratch(gd_graph *g, const int32_t *cnt, bool per_edge) {
     Workspace &w = g->ws;
     const int32_t nh = cnt[C_HUB];
     int rc;
-    if (!per_edge && !w.pull_mask) {
-        // hub masks of the pull form (global counts); zero at rest, cleared
-        // here once and by every pull batch after use
+    if (!w.pull_mask) {
+        // hub masks of the pull form; zero at rest, cleared here once and by
+        // every pull batch after use
         // a node of degree >= 64 takes at least 64 slots: at most nnz / 64 of
         // them, with at most nnz / 1024 further chunks; a node of several
         // chunks has degree > 1024

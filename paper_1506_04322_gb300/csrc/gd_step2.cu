@@ -1544,6 +1544,15 @@ __device__ __forceinline__ unsigned long long plane_pairs(const unsigned long lo
     return (s2 - s1) >> 1;
 }
 
+// counter i out of L bit planes
+template <int L>
+__device__ __forceinline__ uint32_t plane_counter(const unsigned long long (&P)[L], int i) {
+    uint32_t x = 0;
+#pragma unroll
+    for (int a0 = 0; a0 < L; a0++) x |= (uint32_t)((P[a0] >> i) & 1ull) << a0;
+    return x;
+}
+
 // the hubs of the batch ranked above y: the first k (hubs in decreasing rank)
 __device__ __forceinline__ unsigned long long hubs_above(int32_t dy, int32_t y, const int32_t *hd,
                                                          const int32_t *hu, int32_t nb) {
@@ -1566,6 +1575,10 @@ __device__ __forceinline__ void pull_hubs_smem(const CycleArgs &a, int32_t h0, i
 
 // A thread per node y of degree < PULL_WARP_DEG; the neighbours' masks are
 // fetched four at a time so that four loads are in flight per thread.
+// TAB (per-edge credits): instead of summing C(cnt, 2), write the counters
+// of at least 2 of the hubs above y into the batch's dense tables (zero at
+// rest), which the credit pass reads as the push form's counts.
+template <bool TAB>
 __global__ void __launch_bounds__(256)
 k_pull_thread(CycleArgs a, int32_t h0, int32_t nb, const unsigned long long *__restrict__ mask) {
     __shared__ int32_t hu[PULL_MAX], hd[PULL_MAX];
@@ -1590,10 +1603,20 @@ k_pull_thread(CycleArgs a, int32_t h0, int32_t nb, const unsigned long long *__r
 #pragma unroll
         for (int i = 1; i < PULL_TPLANES; i++) any |= P[i];
         if (!any) continue;                   // every counter <= 1
-        c4 += plane_pairs<PULL_TPLANES>(P, hubs_above(d, y, hd, hu, nb));
+        const unsigned long long V = hubs_above(d, y, hd, hu, nb);
+        if constexpr (TAB) {
+            for (unsigned long long mm = any & V; mm; mm &= mm - 1) {
+                const int i = __ffsll((long long)mm) - 1;
+                a.tables[(int64_t)i * a.n + y] = plane_counter<PULL_TPLANES>(P, i);
+            }
+        } else {
+            c4 += plane_pairs<PULL_TPLANES>(P, V);
+        }
     }
-    c4 = warp_sum(c4);
-    if (lane_id() == 0 && c4) add_u128(a.sums + 2 * (S_NUM + X_C4), 4 * c4);
+    if constexpr (!TAB) {
+        c4 = warp_sum(c4);
+        if (lane_id() == 0 && c4) add_u128(a.sums + 2 * (S_NUM + X_C4), 4 * c4);
+    }
 }
 
 // Nodes of degree >= PULL_WARP_DEG are split into chunks of at most
@@ -1621,6 +1644,7 @@ __global__ void k_pull_items(int32_t n, const int32_t *__restrict__ rp, PullItem
     }
 }
 
+template <bool TAB>
 __global__ void __launch_bounds__(256)
 k_pull_warp(CycleArgs a, int32_t h0, int32_t nb, const unsigned long long *__restrict__ mask,
             const PullItem *__restrict__ items, int32_t nitems, uint32_t *heavy_cnt) {
@@ -1666,7 +1690,16 @@ k_pull_warp(CycleArgs a, int32_t h0, int32_t nb, const unsigned long long *__res
             }
         }
         if (t.heavy < 0) {
-            if (lane == 0) c4 += plane_pairs<PULL_CPLANES>(P, hubs_above(d, t.y, hd, hu, nb));
+            if constexpr (TAB) {
+                // lane l: hubs l and l + 32
+                const unsigned long long V = hubs_above(d, t.y, hd, hu, nb);
+                const uint32_t x0 = plane_counter<PULL_CPLANES>(P, lane);
+                const uint32_t x1 = plane_counter<PULL_CPLANES>(P, lane + 32);
+                if (x0 > 1 && ((V >> lane) & 1ull)) a.tables[(int64_t)lane * a.n + t.y] = x0;
+                if (x1 > 1 && ((V >> (lane + 32)) & 1ull)) a.tables[(int64_t)(lane + 32) * a.n + t.y] = x1;
+            } else {
+                if (lane == 0) c4 += plane_pairs<PULL_CPLANES>(P, hubs_above(d, t.y, hd, hu, nb));
+            }
         } else {
             // lane l: counters of hubs l and l + 32 out of the planes
             uint32_t x0 = 0, x1 = 0;
@@ -1680,11 +1713,15 @@ k_pull_warp(CycleArgs a, int32_t h0, int32_t nb, const unsigned long long *__res
             if (x1) atomicAdd(hc + lane + 32, x1);
         }
     }
-    c4 = warp_sum(c4);
-    if (lane == 0 && c4) add_u128(a.sums + 2 * (S_NUM + X_C4), 4 * c4);
+    if constexpr (!TAB) {
+        c4 = warp_sum(c4);
+        if (lane == 0 && c4) add_u128(a.sums + 2 * (S_NUM + X_C4), 4 * c4);
+    }
 }
 
-// heavy nodes: sum C(cnt, 2) over the hubs above y, and reset the counters
+// heavy nodes: sum C(cnt, 2) over the hubs above y (TAB: write those of at
+// least 2 into the tables), and reset the counters
+template <bool TAB>
 __global__ void k_pull_heavy(CycleArgs a, int32_t h0, int32_t nb, const int32_t *__restrict__ heavy_y,
                              int32_t nheavy, uint32_t *heavy_cnt) {
     __shared__ int32_t hu[PULL_MAX], hd[PULL_MAX];
@@ -1699,14 +1736,21 @@ __global__ void k_pull_heavy(CycleArgs a, int32_t h0, int32_t nb, const int32_t 
         const uint32_t x0 = hc[lane], x1 = hc[lane + 32];
         hc[lane] = 0;
         hc[lane + 32] = 0;
-        unsigned long long t = 0;
-        if ((V >> lane) & 1ull) t += c2(x0);
-        if ((V >> (lane + 32)) & 1ull) t += c2(x1);
-        t = warp_sum(t);
-        if (lane == 0) c4 += t;
+        if constexpr (TAB) {
+            if (x0 > 1 && ((V >> lane) & 1ull)) a.tables[(int64_t)lane * a.n + y] = x0;
+            if (x1 > 1 && ((V >> (lane + 32)) & 1ull)) a.tables[(int64_t)(lane + 32) * a.n + y] = x1;
+        } else {
+            unsigned long long t = 0;
+            if ((V >> lane) & 1ull) t += c2(x0);
+            if ((V >> (lane + 32)) & 1ull) t += c2(x1);
+            t = warp_sum(t);
+            if (lane == 0) c4 += t;
+        }
     }
-    c4 = warp_sum(c4);
-    if (lane == 0 && c4) add_u128(a.sums + 2 * (S_NUM + X_C4), 4 * c4);
+    if constexpr (!TAB) {
+        c4 = warp_sum(c4);
+        if (lane == 0 && c4) add_u128(a.sums + 2 * (S_NUM + X_C4), 4 * c4);
+    }
 }
 
 // per-hub wedge work at the hub boundaries of the flat prefix
@@ -2033,49 +2077,73 @@ cudaError_t run_cycles(gd_graph *g, bool per_edge, const int32_t *cnt) {
     }
     int32_t first_push = 0;
     const int pull = g->ctx->opt.hub_pull;
-    if (!per_edge && nh > 0 && w.pull_mask && pull != GD_PULL_NEVER) {
-        // global counts: the heaviest hubs, 64 at a time, in pull form while
-        // a batch's wedges are at least half the CSR slots (a pull pass reads
-        // every slot once; a push pass updates a counter per wedge and clears
-        // its dense tables)
-        std::vector<int64_t> hw(nh + 1);
+    std::vector<int64_t> hw;
+    int32_t pc[2] = {0, 0};
+    PullItem *items = reinterpret_cast<PullItem *>(w.pull_items);
+    const unsigned grid_f = grid_for(std::max<int64_t>(w.hub_flat, 1), 256, sms * 8);
+    if (nh > 0 && w.pull_mask && pull != GD_PULL_NEVER) {
+        // per-hub wedge work, and the chunks of the nodes of degree >=
+        // PULL_WARP_DEG (once per count)
+        hw.resize((size_t)nh + 1);
         GD_LAUNCH(g, "k_hub_work", k_hub_work, grid_for(nh + 1, 256, sms * 4), 256, 0, nh,
                   (const int64_t *)w.hub_off, (const int64_t *)w.hub_pre, w.scan_tmp);
         e = cudaMemcpyAsync(hw.data(), w.scan_tmp, sizeof(int64_t) * (size_t)(nh + 1), cudaMemcpyDeviceToHost, g->stream);
-        if (!e) e = cudaStreamSynchronize(g->stream);
-        if (e) return e;
-        // the chunks of the nodes of degree >= PULL_WARP_DEG (once per count)
-        int32_t pc[2] = {0, 0};
-        PullItem *items = reinterpret_cast<PullItem *>(w.pull_items);
-        e = cudaMemsetAsync(w.pull_counts, 0, 2 * sizeof(int32_t), g->stream);
+        if (!e) e = cudaMemsetAsync(w.pull_counts, 0, 2 * sizeof(int32_t), g->stream);
         if (e) return e;
         GD_LAUNCH(g, "k_pull_items", k_pull_items, grid_for(g->n, 256, sms * 8), 256, 0, g->n, g->rp, items,
                   w.pull_heavy_y, w.pull_counts);
         e = cudaMemcpyAsync(pc, w.pull_counts, sizeof(pc), cudaMemcpyDeviceToHost, g->stream);
         if (!e) e = cudaStreamSynchronize(g->stream);
         if (e) return e;
+    }
+    // one pull pass for hubs [h0, h0 + nb): masks set, counted, masks cleared;
+    // TAB writes the per-hub counters into the batch's tables
+    auto pull_batch = [&](int32_t h0, int32_t nb, bool tab) -> cudaError_t {
+        const unsigned long long *mk = w.pull_mask;
+        GD_LAUNCH(g, "k_pull_mark", k_pull_mark<true>, grid_f, 256, 0, a, h0, nb, w.pull_mask);
+        if (tab) GD_LAUNCH(g, "k_pull_thread", k_pull_thread<true>, (unsigned)(sms * 8), 256, 0, a, h0, nb, mk);
+        else GD_LAUNCH(g, "k_pull_thread", k_pull_thread<false>, (unsigned)(sms * 8), 256, 0, a, h0, nb, mk);
+        if (pc[0] > 0) {
+            const unsigned gr = grid_for((int64_t)pc[0] * 32, 256, sms * 8);
+            if (tab) GD_LAUNCH(g, "k_pull_warp", k_pull_warp<true>, gr, 256, 0, a, h0, nb, mk, (const PullItem *)items,
+                               pc[0], w.pull_heavy_cnt);
+            else GD_LAUNCH(g, "k_pull_warp", k_pull_warp<false>, gr, 256, 0, a, h0, nb, mk, (const PullItem *)items,
+                           pc[0], w.pull_heavy_cnt);
+        }
+        if (pc[1] > 0) {
+            const unsigned gr = grid_for((int64_t)pc[1] * 32, 256, sms * 8);
+            if (tab) GD_LAUNCH(g, "k_pull_heavy", k_pull_heavy<true>, gr, 256, 0, a, h0, nb,
+                               (const int32_t *)w.pull_heavy_y, pc[1], w.pull_heavy_cnt);
+            else GD_LAUNCH(g, "k_pull_heavy", k_pull_heavy<false>, gr, 256, 0, a, h0, nb,
+                           (const int32_t *)w.pull_heavy_y, pc[1], w.pull_heavy_cnt);
+        }
+        GD_LAUNCH(g, "k_pull_clear", k_pull_mark<false>, grid_f, 256, 0, a, h0, nb, w.pull_mask);
+        return cudaGetLastError();
+    };
+    if (!per_edge && !hw.empty()) {
+        // global counts: the heaviest hubs, 64 at a time, in pull form while
+        // a batch's wedges are at least half the CSR slots (a pull pass reads
+        // every slot once; a push pass updates a counter per wedge and clears
+        // its dense tables)
         while (first_push < nh) {
             const int32_t nb = std::min<int32_t>(PULL_MAX, nh - first_push);
             if (pull == GD_PULL_AUTO && hw[first_push + nb] - hw[first_push] < g->nnz / 2) break;
-            const unsigned grid_f = grid_for(w.hub_flat, 256, sms * 8);
-            GD_LAUNCH(g, "k_pull_mark", k_pull_mark<true>, grid_f, 256, 0, a, first_push, nb, w.pull_mask);
-            GD_LAUNCH(g, "k_pull_thread", k_pull_thread, (unsigned)(sms * 8), 256, 0, a, first_push, nb,
-                      (const unsigned long long *)w.pull_mask);
-            if (pc[0] > 0)
-                GD_LAUNCH(g, "k_pull_warp", k_pull_warp, grid_for((int64_t)pc[0] * 32, 256, sms * 8), 256, 0, a,
-                          first_push, nb, (const unsigned long long *)w.pull_mask, (const PullItem *)items, pc[0],
-                          w.pull_heavy_cnt);
-            if (pc[1] > 0)
-                GD_LAUNCH(g, "k_pull_heavy", k_pull_heavy, grid_for((int64_t)pc[1] * 32, 256, sms * 8), 256, 0, a,
-                          first_push, nb, (const int32_t *)w.pull_heavy_y, pc[1], w.pull_heavy_cnt);
-            GD_LAUNCH(g, "k_pull_clear", k_pull_mark<false>, grid_f, 256, 0, a, first_push, nb, w.pull_mask);
+            if ((e = pull_batch(first_push, nb, false))) return e;
             first_push += nb;
         }
     }
     for (int32_t h0 = first_push; h0 < nh; h0 += B) {
         a.hub0 = h0;
         a.nhub = nh - h0 < B ? nh - h0 : B;
-        GD_LAUNCH(g, "k_cycles_hub_count", k_cycles_hub<0>, (unsigned)(sms * 8), 256, 0, a);
+        // per-edge credits need the batch's counters in its tables: counted in
+        // pull form when the batch's wedges are at least twice the CSR slots
+        const bool tab_pull = per_edge && !hw.empty() &&
+                              (pull == GD_PULL_ALWAYS || hw[h0 + a.nhub] - hw[h0] >= 2 * g->nnz);
+        if (tab_pull) {
+            if ((e = pull_batch(h0, a.nhub, true))) return e;
+        } else {
+            GD_LAUNCH(g, "k_cycles_hub_count", k_cycles_hub<0>, (unsigned)(sms * 8), 256, 0, a);
+        }
         if (per_edge) GD_LAUNCH(g, "k_cycles_hub_credit", k_cycles_hub<1>, (unsigned)(sms * 8), 256, 0, a);
         if (per_edge) GD_LAUNCH(g, "k_cycles_hub_clear", k_cycles_hub_clear<true>, (unsigned)(sms * 4), 256, 0, a);
         else GD_LAUNCH(g, "k_cycles_hub_clear", k_cycles_hub_clear<false>, (unsigned)(sms * 4), 256, 0, a);
