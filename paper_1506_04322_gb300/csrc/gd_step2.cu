@@ -10,7 +10,9 @@
 //   tiers     vertices by wedge work W(u) = sum_{v in N(u), v below u} d_v.
 //
 // Triangles and 4-cliques ("bitmap" kernels).  For every node a, a team (a
-// warp for |N+(a)| <= 64, a CTA up to 1024, a CTA on global scratch above)
+// warp for |N+(a)| <= 64, a CTA of 256 threads up to 256, of 1024 threads up
+// to 1024 -- its 128 KB bit matrix allows one CTA per SM, so all 32 warps of
+// that CTA share the node --, a CTA on global scratch above)
 // walks the pairs (c, x) with c in N+(a) and x in N+(c), the concatenated
 // out-lists spread evenly over the team's warps; a shared-memory filter and
 // hash table of N+(a) decide membership, candidates queued 32 at a time.  A
@@ -1917,7 +1919,7 @@ static cudaError_t launch_clique_buckets(gd_graph *g, const int32_t *cnt) {
     cudaError_t e;
     if ((e = launch_clique<CL_D0, 256, true, MODE>(g, 0, cnt[C_CL0]))) return e;
     if ((e = launch_clique<CL_D1, 256, false, MODE>(g, 1, cnt[C_CL0 + 1]))) return e;
-    if ((e = launch_clique<CL_D2, 512, false, MODE>(g, 2, cnt[C_CL0 + 2]))) return e;
+    if ((e = launch_clique<CL_D2, 1024, false, MODE>(g, 2, cnt[C_CL0 + 2]))) return e;
     return launch_clique<0, CL_BIG_THREADS, false, MODE>(g, 3, cnt[C_CL0 + 3]);
 }
 
@@ -1943,7 +1945,7 @@ cudaError_t clique_pairs_bytes(gd_graph *g, const int32_t *cnt, size_t *need) {
     cudaError_t e;
     if ((e = pairs_need<CL_D0, 256, true>(g, cnt[C_CL0], need))) return e;
     if ((e = pairs_need<CL_D1, 256, false>(g, cnt[C_CL0 + 1], need))) return e;
-    return pairs_need<CL_D2, 512, false>(g, cnt[C_CL0 + 2], need);
+    return pairs_need<CL_D2, 1024, false>(g, cnt[C_CL0 + 2], need);
 }
 
 // Flat row offsets of all hubs (hub_off, nh + 1 entries); *flat receives
