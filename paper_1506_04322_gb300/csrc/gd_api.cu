@@ -581,6 +581,10 @@ void gd_destroy(gd_ctx *ctx) {
     for (auto &r : ctx->recs) { ctx->evpool.push_back(r.a); ctx->evpool.push_back(r.b); }
     for (cudaEvent_t ev : ctx->evpool) cudaEventDestroy(ev);
     if (ctx->stream) cudaStreamDestroy(ctx->stream);
+    for (int i = 0; i < gd_ctx::COPY_STREAMS; i++)
+        if (ctx->copy_st[i]) cudaStreamDestroy(ctx->copy_st[i]);
+    for (int i = 0; i <= gd_ctx::COPY_STREAMS; i++)
+        if (ctx->copy_ev[i]) cudaEventDestroy(ctx->copy_ev[i]);
     delete ctx;
 }
 
@@ -795,8 +799,28 @@ int gd_count_per_edge(gd_graph *g, uint64_t *out, int out_flags, gd_u128 global_
     }
     rc = count_path(g, true, dst);
     if (rc) return rc;
-    if (!dev_out && g->m > 0)
-        GD_CK(ctx, cudaMemcpyAsync(out, dst, out_bytes, cudaMemcpyDeviceToHost, g->stream));
+    if (!dev_out && g->m > 0) {
+        // the matrix back to the host in chunks on several streams at once
+        // (more copy engines at work than one stream's copy gets); the
+        // graph's stream waits for all of them before the results are read
+        constexpr int K = gd_ctx::COPY_STREAMS;
+        if (!ctx->copy_st[0]) {
+            for (int i = 0; i < K; i++)
+                GD_CK(ctx, cudaStreamCreateWithFlags(&ctx->copy_st[i], cudaStreamNonBlocking));
+            for (int i = 0; i <= K; i++) GD_CK(ctx, cudaEventCreateWithFlags(&ctx->copy_ev[i], cudaEventDisableTiming));
+        }
+        GD_CK(ctx, cudaEventRecord(ctx->copy_ev[K], g->stream));
+        const size_t rows = (size_t)g->m, per = (rows + K - 1) / K;
+        for (int i = 0; i < K; i++) {
+            const size_t r0 = std::min(rows, per * (size_t)i), r1 = std::min(rows, per * (size_t)(i + 1));
+            GD_CK(ctx, cudaStreamWaitEvent(ctx->copy_st[i], ctx->copy_ev[K], 0));
+            if (r1 > r0)
+                GD_CK(ctx, cudaMemcpyAsync(out + r0 * 15, dst + r0 * 15, sizeof(uint64_t) * 15 * (r1 - r0),
+                                           cudaMemcpyDeviceToHost, ctx->copy_st[i]));
+            GD_CK(ctx, cudaEventRecord(ctx->copy_ev[i], ctx->copy_st[i]));
+            GD_CK(ctx, cudaStreamWaitEvent(g->stream, ctx->copy_ev[i], 0));
+        }
+    }
     return read_results(g, global_out);
 }
 

@@ -179,6 +179,10 @@ struct gd_ctx {
     // captured batch pipeline
     gdi::BatchGraph *bgraph = nullptr;
     gdi::GatherBufs gather;
+    // per-edge output copied to the host in chunks on several streams at once
+    static constexpr int COPY_STREAMS = 4;
+    cudaStream_t copy_st[COPY_STREAMS] = {};
+    cudaEvent_t copy_ev[COPY_STREAMS + 1] = {};
 };
 
 struct gd_graph {
