@@ -177,7 +177,8 @@ KERNEL_FAMILIES = {
 PULL_MAX = 64
 
 
-def algorithmic_bytes(g, triangles: int, per_edge: bool, pull_batches: int = 0, hub_log2: int = 17) -> dict:
+def algorithmic_bytes(g, triangles: int, per_edge: bool, pull_batches: int = 0, hub_log2: int = 17,
+                      hub_batch: int = 16) -> dict:
     """Bytes each kernel family must move for this graph, per step (4-byte
     ids, degrees and |Tri| counters, 8-byte credits and masks).  Nodes are
     ranked by (degree, id); a -> c orients every edge from the lower-ranked
@@ -196,10 +197,13 @@ def algorithmic_bytes(g, triangles: int, per_edge: bool, pull_batches: int = 0, 
       wedge (y ranked below u; L wedges, 4 B).  The per-edge credit pass
       repeats the scan, reads each live counter (4 B), credits (v,y) (8 B)
       and credits each (u,v) once (8 B).
-    cycles, pull form (global counts, the first pull_batches batches of 64
-      hubs in decreasing rank): per batch every CSR slot read once with its
+    cycles, pull form (hub batches in decreasing rank: for global counts the
+      first pull_batches batches of 64 hubs; for per-edge credits the batches
+      of `hub_batch` hubs with at least 2 nnz wedges, whose counts the pull
+      writes into the tables): per batch every CSR slot read once with its
       neighbour's 8-byte mask (12 B per slot), and the hubs' lists marked and
-      cleared (24 B per entry); their wedges leave the push terms.
+      cleared (24 B per entry); their wedges leave the push terms of the count
+      pass (the per-edge credit pass walks every wedge as before).
     """
     d = g.degrees().astype(np.int64)
     n = g.n
@@ -223,19 +227,27 @@ def algorithmic_bytes(g, triangles: int, per_edge: bool, pull_batches: int = 0, 
     Lu = np.bincount(cu[upk], weights=pos[upk], minlength=n).astype(np.int64)
     W, L = int(Wu.sum()), int(Lu.sum())
     pull_bytes, Wp, Lp = 0, 0, 0
-    if pull_batches and not per_edge:
+    if pull_batches:
         thr = max(1 << hub_log2, n // 8)
         hubs = np.flatnonzero(Wu > thr)
-        hubs = hubs[np.lexsort((-hubs, -d[hubs]))][:PULL_MAX * pull_batches]
+        hubs = hubs[np.lexsort((-hubs, -d[hubs]))]
+        if per_edge:
+            batches = [hubs[i:i + hub_batch] for i in range(0, len(hubs), hub_batch)]
+            pulled = [b for b in batches if int(Wu[b].sum()) >= 2 * len(cols)]
+            hubs = np.concatenate(pulled) if pulled else hubs[:0]
+            npull = len(pulled)
+        else:
+            hubs = hubs[:PULL_MAX * pull_batches]
+            npull = pull_batches
         Wp, Lp = int(Wu[hubs].sum()), int(Lu[hubs].sum())
-        pull_bytes = pull_batches * 12 * len(cols) + 24 * int(d[hubs].sum())
+        pull_bytes = npull * 12 * len(cols) + 24 * int(d[hubs].sum())
     passes = 2 if per_edge else 1
     bitmap = passes * (12 * m + 4 * X) + triangles * (20 + (36 if per_edge else 0))
     cycles = 16 * m + 8 * (W - Wp) + 4 * (L - Lp) + pull_bytes
     if per_edge:
         cycles += 16 * m + 8 * W + 12 * L + 8 * m
     return {"bitmap": bitmap, "cycles": cycles, "W": W, "L": L, "X": X, "m": m,
-            "pulled_hub_wedges": Wp, "pull_batches": pull_batches}
+            "pulled_hub_wedges": Wp, "pull_batches": npull if pull_batches else 0}
 
 
 def source_digest() -> str:
@@ -746,7 +758,10 @@ def measure_workload(gd, torch, ctx, g, device, global_only: bool, steps: int, w
                   for f, names in KERNEL_FAMILIES.items()}
         dom = max(fam_ms, key=fam_ms.get)
         pull_batches = kern.get("k_pull_thread", {"launches": 0})["launches"] // steps
-        ab = algorithmic_bytes(g, int(glob[0]), not global_only, pull_batches, hub_log2)
+        hub_batch = max(1, min(16, (64 << 20) // (4 * max(g.n, 1))))
+        ab = algorithmic_bytes(g, int(glob[0]), not global_only, pull_batches, hub_log2, hub_batch)
+        if ab["pull_batches"] != pull_batches:
+            raise RuntimeError("the byte model's pulled batches differ from the launched ones")
         achieved = ab[dom] / (fam_ms[dom] / 1000.0) / 1e9
         rec["roofline"] = {
             "kernel": dom, "kernels": [k for k in KERNEL_FAMILIES[dom] if k in kern], "bound": "hbm",
