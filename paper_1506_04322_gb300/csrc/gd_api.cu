@@ -353,7 +353,7 @@ int ensure_medium_scratch(gd_graph *g, const int32_t *cnt) {
 
 // Flat neighbour lists of the hubs: row offsets (from the hub list), then
 // lengths, prefix and scan scratch sized to the hubs' concatenated rows.
-int ensure_hub_scratch(gd_graph *g, const int32_t *cnt, bool per_edge) {
+int ensure_hub_scratch(gd_graph *g, const int32_t *cnt) {
     Workspace &w = g->ws;
     const int32_t nh = cnt[C_HUB];
     int rc;
@@ -749,7 +749,7 @@ static int count_path(gd_graph *g, bool per_edge, uint64_t *out_dev) {
     int32_t cnt[C_NUM];
     GD_CK(ctx, run_schedule(g, cnt));
     if (cnt[C_CL0 + 3] > 0 && (rc = ensure_clique_scratch(g, cnt))) return rc;
-    if (cnt[C_HUB] > 0 && (rc = ensure_hub_scratch(g, cnt, per_edge))) return rc;
+    if (cnt[C_HUB] > 0 && (rc = ensure_hub_scratch(g, cnt))) return rc;
     if (cnt[C_MEDIUM] > 0 && (rc = ensure_medium_scratch(g, cnt))) return rc;
     if ((rc = ensure_pairs(g, cnt))) return rc;
     if (per_edge) {
