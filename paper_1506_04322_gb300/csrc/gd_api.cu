@@ -331,7 +331,7 @@ int ensure_records(gd_graph *g, int64_t total) {
 }
 
 // Per-CTA tables of the medium tier: a power of two >= 2 W entries for the
-// largest medium vertex, one per CTA (two per SM, fewer when there are fewer
+// largest medium vertex (a vertex uses the first 1.5 W + 1024 or fewer), one per CTA (two per SM, fewer when there are fewer
 // vertices or the tables would pass medium_table_limit), all entries empty
 // (all ones).
 int ensure_medium_scratch(gd_graph *g, const int32_t *cnt) {
