@@ -1555,16 +1555,35 @@ __global__ void k_pull_mark(CycleArgs a, int32_t h0, int32_t nb, unsigned long l
     }
 }
 
-// add a mask into the lowest LA planes (the caller guarantees that no
-// counter passes 2^LA - 1 on the way)
+// carry-save adder: a + b + c = l + 2 h, in each of the 64 bit positions
+__device__ __forceinline__ void csa(unsigned long long &h, unsigned long long &l, unsigned long long a,
+                                    unsigned long long b, unsigned long long c) {
+    const unsigned long long u = a ^ b;
+    h = (a & b) | (u & c);
+    l = u ^ c;
+}
+
+// add eight masks into the lowest LA planes (Harley-Seal): the masks pass
+// through carry-save adders into the ones, twos and fours planes, and only
+// the eights carry ripples through the planes above; about 5.5 logic
+// operations a mask where a ripple of each mask costs 2 LA.  The caller
+// guarantees that no counter passes 2^LA - 1.
 template <int LA, int L>
-__device__ __forceinline__ void plane_add(unsigned long long (&P)[L], unsigned long long x) {
-    static_assert(LA <= L, "active planes");
+__device__ __forceinline__ void plane_add8(unsigned long long (&P)[L], const unsigned long long (&m)[8]) {
+    static_assert(LA >= 4 && LA <= L, "active planes");
+    unsigned long long t2a, t2b, t4a, t4b, t8;
+    csa(t2a, P[0], P[0], m[0], m[1]);
+    csa(t2b, P[0], P[0], m[2], m[3]);
+    csa(t4a, P[1], P[1], t2a, t2b);
+    csa(t2a, P[0], P[0], m[4], m[5]);
+    csa(t2b, P[0], P[0], m[6], m[7]);
+    csa(t4b, P[1], P[1], t2a, t2b);
+    csa(t8, P[2], P[2], t4a, t4b);
 #pragma unroll
-    for (int b = 0; b < LA; b++) {
-        const unsigned long long c = P[b] & x;
-        P[b] ^= x;
-        x = c;
+    for (int b = 3; b < LA; b++) {
+        const unsigned long long c = P[b] & t8;
+        P[b] ^= t8;
+        t8 = c;
     }
 }
 
@@ -1614,7 +1633,8 @@ __device__ __forceinline__ void pull_hubs_smem(const CycleArgs &a, int32_t h0, i
 }
 
 // A thread per node y of degree < PULL_WARP_DEG; the neighbours' masks are
-// fetched four at a time so that four loads are in flight per thread.
+// fetched eight at a time (eight loads in flight per thread) and added by
+// carry-save adders.
 // TAB (per-edge credits): instead of summing C(cnt, 2), write the counters
 // of at least 2 of the hubs above y into the batch's dense tables (zero at
 // rest), which the credit pass reads as the push form's counts.
@@ -1628,17 +1648,16 @@ k_pull_thread(CycleArgs a, int32_t h0, int32_t nb, const unsigned long long *__r
         const int32_t b = __ldg(a.rp + y), e = __ldg(a.rp + y + 1), d = e - b;
         if (d < 2 || d >= PULL_WARP_DEG) continue;
         unsigned long long P[PULL_TPLANES] = {0, 0, 0, 0, 0, 0, 0};
-        int32_t p = b;
-        for (; p + 4 <= e; p += 4) {
-            const int32_t v0 = __ldg(a.ci + p), v1 = __ldg(a.ci + p + 1);
-            const int32_t v2 = __ldg(a.ci + p + 2), v3 = __ldg(a.ci + p + 3);
-            const unsigned long long m0 = mask[v0], m1 = mask[v1], m2 = mask[v2], m3 = mask[v3];
-            plane_add<PULL_TPLANES, PULL_TPLANES>(P, m0);
-            plane_add<PULL_TPLANES, PULL_TPLANES>(P, m1);
-            plane_add<PULL_TPLANES, PULL_TPLANES>(P, m2);
-            plane_add<PULL_TPLANES, PULL_TPLANES>(P, m3);
+        for (int32_t p = b; p < e; p += 8) {
+            // eight masks at a time (zero past the end), their loads in flight together
+            int32_t v[8];
+            unsigned long long m[8];
+#pragma unroll
+            for (int j = 0; j < 8; j++) v[j] = p + j < e ? __ldg(a.ci + p + j) : -1;
+#pragma unroll
+            for (int j = 0; j < 8; j++) m[j] = v[j] >= 0 ? mask[v[j]] : 0ull;
+            plane_add8<PULL_TPLANES, PULL_TPLANES>(P, m);
         }
-        for (; p < e; p++) plane_add<PULL_TPLANES, PULL_TPLANES>(P, mask[__ldg(a.ci + p)]);
         unsigned long long any = 0;
 #pragma unroll
         for (int i = 1; i < PULL_TPLANES; i++) any |= P[i];
@@ -1699,17 +1718,16 @@ k_pull_warp(CycleArgs a, int32_t h0, int32_t nb, const unsigned long long *__res
         unsigned long long P[PULL_CPLANES];
 #pragma unroll
         for (int i = 0; i < PULL_CPLANES; i++) P[i] = 0;
-        int32_t p = b + lane;
-        for (; p + 3 * WARP < e; p += 4 * WARP) {
-            const int32_t v0 = __ldg(a.ci + p), v1 = __ldg(a.ci + p + WARP);
-            const int32_t v2 = __ldg(a.ci + p + 2 * WARP), v3 = __ldg(a.ci + p + 3 * WARP);
-            const unsigned long long m0 = mask[v0], m1 = mask[v1], m2 = mask[v2], m3 = mask[v3];
-            plane_add<PULL_LPLANES, PULL_CPLANES>(P, m0);
-            plane_add<PULL_LPLANES, PULL_CPLANES>(P, m1);
-            plane_add<PULL_LPLANES, PULL_CPLANES>(P, m2);
-            plane_add<PULL_LPLANES, PULL_CPLANES>(P, m3);
+        for (int32_t p = b + lane; p < e; p += 8 * WARP) {
+            // this lane's next eight masks (zero past the end), loads in flight together
+            int32_t v[8];
+            unsigned long long m[8];
+#pragma unroll
+            for (int j = 0; j < 8; j++) v[j] = p + j * WARP < e ? __ldg(a.ci + p + j * WARP) : -1;
+#pragma unroll
+            for (int j = 0; j < 8; j++) m[j] = v[j] >= 0 ? mask[v[j]] : 0ull;
+            plane_add8<PULL_LPLANES, PULL_CPLANES>(P, m);
         }
-        for (; p < e; p += WARP) plane_add<PULL_LPLANES, PULL_CPLANES>(P, mask[__ldg(a.ci + p)]);
         unsigned long long any = 0;
 #pragma unroll
         for (int i = 0; i < PULL_LPLANES; i++) any |= P[i];
