@@ -923,6 +923,65 @@ __device__ __forceinline__ void walk_range(const CycleArgs &a, int32_t u, int32_
     }
 }
 
+// walk_range with two wedges per lane at a time (w0 + lane and w0 + 32 +
+// lane), so that their table probes can be in flight together:
+// f2(k0, q0, y0, ok0, live0, k1, q1, y1, ok1, live1), each half a 32-wedge
+// group as in walk_range.
+template <typename F2, typename G>
+__device__ __forceinline__ void walk_range2(const CycleArgs &a, int32_t u, int32_t bu, int32_t du,
+                                            const long long *pre, long long w_lo, long long w_hi, F2 f2, G flush) {
+    if (w_lo >= w_hi) return;
+    const int lane = lane_id();
+    int32_t lo = 0, hi = du;
+    while (lo < hi) {
+        const int32_t mid = (lo + hi + 1) >> 1;
+        if (pre[mid] <= w_lo) lo = mid; else hi = mid - 1;
+    }
+    for (int32_t j0 = lo; j0 < du && pre[j0] < w_hi; j0 += WARP) {
+        const int32_t j = j0 + lane;
+        int32_t len = 0, start = 0;
+        if (j < du) {
+            const long long p0 = pre[j], p1 = pre[j + 1];
+            const long long s0 = max(p0, w_lo), e0 = min(p1, w_hi);
+            if (e0 > s0) {
+                len = (int32_t)(e0 - s0);
+                start = a.rp[a.ci[bu + j]] + (int32_t)(s0 - p0);
+            }
+        }
+        const int32_t incl = warp_incl_scan(len);
+        const int32_t total = __shfl_sync(FULL, incl, 31);
+        const int32_t excl = incl - len;
+        for (int32_t w0 = 0; w0 < total; w0 += 2 * WARP) {
+            int32_t k[2], q[2], y[2];
+            bool ok[2], live[2];
+#pragma unroll
+            for (int h = 0; h < 2; h++) {
+                const int32_t w = w0 + h * WARP + lane;
+                int32_t kk = 0;
+#pragma unroll
+                for (int s = 16; s >= 1; s >>= 1) {
+                    const int32_t e = __shfl_sync(FULL, excl, kk + s);
+                    if (e <= w) kk += s;
+                }
+                const int32_t ks = __shfl_sync(FULL, start, kk);
+                const int32_t ke = __shfl_sync(FULL, excl, kk);
+                k[h] = kk;
+                live[h] = w < total;
+                ok[h] = false;
+                q[h] = 0;
+                y[h] = 0;
+                if (live[h]) {
+                    q[h] = ks + (w - ke);
+                    y[h] = a.ci[q[h]];
+                    ok[h] = precedes(a.nd[q[h]], y[h], du, u);
+                }
+            }
+            f2(k[0], q[0], y[0], ok[0], live[0], k[1], q[1], y[1], ok[1], live[1]);
+        }
+        flush(j);
+    }
+}
+
 // Wedge prefix of the small tier in shared memory: vertices of larger
 // degree walk their neighbours 32 at a time per warp instead.
 constexpr int SMALL_PCAP = 2048;
@@ -1138,12 +1197,47 @@ __device__ __forceinline__ uint32_t mh_get(const unsigned long long *t, uint32_t
     return 0;
 }
 
+// mh_add for two keys (each only if its ok): both home slots are loaded
+// together and, in the common cases (the key is there, or the slot is
+// empty), both atomics are issued before either result is used; any other
+// case finishes through mh_add.  o0, o1: the previous counts as in mh_add.
+__device__ __forceinline__ void mh_add2(unsigned long long *t, uint32_t cap, int32_t y0, bool ok0, int32_t y1,
+                                        bool ok1, uint32_t &o0, uint32_t &o1) {
+    const unsigned long long k0 = (unsigned long long)(uint32_t)y0 << 32, k1 = (unsigned long long)(uint32_t)y1 << 32;
+    const uint32_t h0 = mh_home(y0, cap), h1 = mh_home(y1, cap);
+    const unsigned long long w0 = ok0 ? __ldcg(t + h0) : 0, w1 = ok1 ? __ldcg(t + h1) : 0;
+    unsigned long long r0 = 0, r1 = 0;
+    int m0 = 0, m1 = 0;                       // 1: insertion tried, 2: increment issued
+    if (ok0) {
+        if (w0 == MH_EMPTY) { r0 = atomicCAS(t + h0, MH_EMPTY, k0 | 1ull); m0 = 1; }
+        else if ((w0 & MH_KEY) == k0) { r0 = atomicAdd(t + h0, 1ull); m0 = 2; }
+    }
+    if (ok1) {
+        if (w1 == MH_EMPTY) { r1 = atomicCAS(t + h1, MH_EMPTY, k1 | 1ull); m1 = 1; }
+        else if ((w1 & MH_KEY) == k1) { r1 = atomicAdd(t + h1, 1ull); m1 = 2; }
+    }
+    o0 = 0;
+    o1 = 0;
+    if (ok0) o0 = m0 == 2 ? (uint32_t)r0 : (m0 == 1 && r0 == MH_EMPTY) ? 0u : mh_add(t, cap, y0);
+    if (ok1) o1 = m1 == 2 ? (uint32_t)r1 : (m1 == 1 && r1 == MH_EMPTY) ? 0u : mh_add(t, cap, y1);
+}
+
+// mh_get for two keys, both home slots loaded together
+__device__ __forceinline__ void mh_get2(const unsigned long long *t, uint32_t cap, int32_t y0, bool ok0, int32_t y1,
+                                        bool ok1, uint32_t &c0, uint32_t &c1) {
+    const unsigned long long k0 = (unsigned long long)(uint32_t)y0 << 32, k1 = (unsigned long long)(uint32_t)y1 << 32;
+    const unsigned long long w0 = ok0 ? __ldcg(t + mh_home(y0, cap)) : MH_EMPTY;
+    const unsigned long long w1 = ok1 ? __ldcg(t + mh_home(y1, cap)) : MH_EMPTY;
+    c0 = (w0 & MH_KEY) == k0 && w0 != MH_EMPTY ? (uint32_t)w0 : w0 == MH_EMPTY ? 0u : mh_get(t, cap, y0);
+    c1 = (w1 & MH_KEY) == k1 && w1 != MH_EMPTY ? (uint32_t)w1 : w1 == MH_EMPTY ? 0u : mh_get(t, cap, y1);
+}
+
 // Wedge prefix of the medium tier in shared memory: vertices of larger
 // degree walk their neighbours 32 at a time per warp instead.
 constexpr int MED_PCAP = 8192;
 
 template <int THREADS, bool CREDIT>
-__global__ void __launch_bounds__(THREADS)
+__global__ void __launch_bounds__(THREADS, 2048 / THREADS)
 k_cycles_medium(CycleArgs a) {
     constexpr int NW = THREADS / 32;
     __shared__ unsigned long long item[NW][WARP];
@@ -1177,15 +1271,32 @@ k_cycles_medium(CycleArgs a) {
             if (c > 1) atomicAdd(a.yacc + q, (unsigned long long)(c - 1));
             item_add(item[warp], k, c > 1 ? c - 1 : 0, live);
         };
+        // the same for two wedges per lane, their probes in flight together
+        auto count2 = [&](int k0, int32_t q0, int32_t y0, bool ok0, bool live0,
+                          int k1, int32_t q1, int32_t y1, bool ok1, bool live1) {
+            uint32_t o0, o1;
+            mh_add2(tab, cap, y0, ok0, y1, ok1, o0, o1);
+            if ((ok0 && o0 == 0xffffffffu) || (ok1 && o1 == 0xffffffffu)) full = true;
+            else if (!CREDIT) c4 += (unsigned long long)o0 + o1;
+        };
+        auto credit2 = [&](int k0, int32_t q0, int32_t y0, bool ok0, bool live0,
+                           int k1, int32_t q1, int32_t y1, bool ok1, bool live1) {
+            uint32_t c0, c1;
+            mh_get2(tab, cap, y0, ok0, y1, ok1, c0, c1);
+            if (c0 > 1) atomicAdd(a.yacc + q0, (unsigned long long)(c0 - 1));
+            if (c1 > 1) atomicAdd(a.yacc + q1, (unsigned long long)(c1 - 1));
+            item_add(item[warp], k0, c0 > 1 ? c0 - 1 : 0, live0);
+            item_add(item[warp], k1, c1 > 1 ? c1 - 1 : 0, live1);
+        };
         if (du <= MED_PCAP) {
             // every warp takes an equal range of the vertex's wedges
             const long long W = wedge_prefix<THREADS>(a, u, bu, du, pre, wsum);
             for (int ph = 0; ph < (CREDIT ? 2 : 1); ph++) {
                 const long long w_lo = W * warp / NW, w_hi = W * (warp + 1) / NW;
                 if (ph == 0) {
-                    walk_range(a, u, bu, du, pre, w_lo, w_hi, count, [&](int32_t) {});
+                    walk_range2(a, u, bu, du, pre, w_lo, w_hi, count2, [&](int32_t) {});
                 } else {
-                    walk_range(a, u, bu, du, pre, w_lo, w_hi, credit, [&](int32_t j) {
+                    walk_range2(a, u, bu, du, pre, w_lo, w_hi, credit2, [&](int32_t j) {
                         __syncwarp();
                         const unsigned long long sv = item[warp][lane];
                         if (sv) { atomicAdd(a.yacc + bu + j, sv); item[warp][lane] = 0; }
@@ -1269,13 +1380,30 @@ k_cycles_medium_cl(CycleArgs a, int32_t nv_big) {
             if (c > 1) atomicAdd(a.yacc + q, (unsigned long long)(c - 1));
             item_add(item[warp], k, c > 1 ? c - 1 : 0, live);
         };
+        // the same for two wedges per lane, their probes in flight together
+        auto count2 = [&](int k0, int32_t q0, int32_t y0, bool ok0, bool live0,
+                          int k1, int32_t q1, int32_t y1, bool ok1, bool live1) {
+            uint32_t o0, o1;
+            mh_add2(tab, cap, y0, ok0, y1, ok1, o0, o1);
+            if ((ok0 && o0 == 0xffffffffu) || (ok1 && o1 == 0xffffffffu)) full = true;
+            else if (!CREDIT) c4 += (unsigned long long)o0 + o1;
+        };
+        auto credit2 = [&](int k0, int32_t q0, int32_t y0, bool ok0, bool live0,
+                           int k1, int32_t q1, int32_t y1, bool ok1, bool live1) {
+            uint32_t c0, c1;
+            mh_get2(tab, cap, y0, ok0, y1, ok1, c0, c1);
+            if (c0 > 1) atomicAdd(a.yacc + q0, (unsigned long long)(c0 - 1));
+            if (c1 > 1) atomicAdd(a.yacc + q1, (unsigned long long)(c1 - 1));
+            item_add(item[warp], k0, c0 > 1 ? c0 - 1 : 0, live0);
+            item_add(item[warp], k1, c1 > 1 ? c1 - 1 : 0, live1);
+        };
         if (du <= MED_PCAP) {
             const long long W = wedge_prefix<THREADS>(a, u, bu, du, pre, wsum);
             const long long w_lo = W * gw / GW, w_hi = W * (gw + 1) / GW;
-            walk_range(a, u, bu, du, pre, w_lo, w_hi, count, [&](int32_t) {});
+            walk_range2(a, u, bu, du, pre, w_lo, w_hi, count2, [&](int32_t) {});
             cl.sync();
             if (CREDIT) {
-                walk_range(a, u, bu, du, pre, w_lo, w_hi, credit, [&](int32_t j) {
+                walk_range2(a, u, bu, du, pre, w_lo, w_hi, credit2, [&](int32_t j) {
                     __syncwarp();
                     const unsigned long long sv = item[warp][lane];
                     if (sv) { atomicAdd(a.yacc + bu + j, sv); item[warp][lane] = 0; }
