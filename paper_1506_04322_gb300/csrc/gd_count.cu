@@ -375,6 +375,7 @@ struct FinalArgs {
     const unsigned long long *qcred;             // per slot: triangle-perimeter credit, then degree-sum credit
     int qr_credits;                              // A_u + A_v and D_T from the credits
     const unsigned long long *cacc, *yacc;
+    const uint32_t *y32;                         // oriented credits as 32-bit words, when so kept
     uint64_t *out;
     unsigned long long *sums;
     int32_t *status;
@@ -434,7 +435,7 @@ __global__ void __launch_bounds__(FINAL_THREADS) k_final(FinalArgs a) {
         }
         if (a.variant != GD_VARIANT_LITERAL) {
             const int32_t q = a.mate[p];
-            c4 = (int64_t)(a.yacc[p] + a.yacc[q]);
+            c4 = a.y32 ? (int64_t)a.y32[p] + a.y32[q] : (int64_t)(a.yacc[p] + a.yacc[q]);
         }
         // A = A_u + A_v and D_T, then the restricted counts summed over both
         // endpoints (the columns need only these sums):
@@ -711,6 +712,7 @@ cudaError_t run_final(gd_graph *g, int variant, bool per_edge, bool cliq_credits
     a.qcred = (const unsigned long long *)w.qcred;
     a.qr_credits = qr_credits ? 1 : 0;
     a.cacc = (const unsigned long long *)w.cacc; a.yacc = (const unsigned long long *)w.yacc;
+    a.y32 = variant != GD_VARIANT_LITERAL && w.yacc32 ? reinterpret_cast<const uint32_t *>(w.yacc) : nullptr;
     a.out = out_dev; a.sums = w.sums; a.status = w.status;
     GD_LAUNCH(g, "k_final", k_final, grid_for(g->m, 256, sms * 8), 256, 0, a);
     return cudaGetLastError();

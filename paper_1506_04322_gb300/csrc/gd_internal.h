@@ -79,6 +79,7 @@ struct Workspace {
     uint64_t *qcred = nullptr;   // [2 nnz] per slot: triangle-perimeter credit, degree-sum credit
     uint64_t *cacc = nullptr;      // [nnz] 4-clique credits per slot
     uint64_t *yacc = nullptr;      // [nnz] 4-cycle credits per slot (or cyc_e for literal)
+    bool yacc32 = false;           // the oriented per-edge credits are uint32 words (max degree <= 65536)
     // schedule
     int32_t *vlist = nullptr;      // [n] small tier from the front, medium tier from the back
     int32_t *hubs = nullptr;       // [n] hub tier

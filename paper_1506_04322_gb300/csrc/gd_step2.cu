@@ -825,6 +825,7 @@ struct CycleArgs {
     int64_t mcap;                // their entries per CTA (power of two)
     const int64_t *west;         // wedges per medium vertex
     unsigned long long *yacc;    // per-slot 4-cycle credits (per-edge mode)
+    uint32_t *y32;               // the same as 32-bit words (non-null when every slot's total fits)
     unsigned long long *sums;    // u128 sums: X_C4 gets sum_e C4(e) = 4 * 4-cycles (global mode)
     int32_t *status;             // error bits
     int32_t hub0, nhub;          // hub batch
@@ -833,6 +834,12 @@ struct CycleArgs {
                                  // prefix, the neighbour's row (k_hub_rows)
     int64_t *hpre;               // [flat + 1] exclusive prefix of hlen (hpre[flat] = batch wedges)
 };
+
+// credit x 4-cycles to slot q
+__device__ __forceinline__ void ycredit(const CycleArgs &a, int64_t q, unsigned long long x) {
+    if (a.y32) atomicAdd(a.y32 + q, (uint32_t)x);
+    else atomicAdd(a.yacc + q, x);
+}
 
 __device__ __forceinline__ unsigned long long c2(uint32_t c) { return (unsigned long long)c * (c - 1) / 2; }
 
@@ -1034,13 +1041,13 @@ k_cycles_tiny(CycleArgs a) {
             warp_wedges(u, du, bu, 0, du, WARP, a.rp, a.ci, a.nd,
                 [&](int k, int32_t q, int32_t y, bool ok, bool live) {
                     const uint32_t c = ok ? sm_find(K, V, TMASK, y) : 0;
-                    if (c > 1) atomicAdd(a.yacc + q, (unsigned long long)(c - 1));
+                    if (c > 1) ycredit(a, q, (unsigned long long)(c - 1));
                     item_add(item[warp], k, c > 1 ? c - 1 : 0, live);
                 },
                 [&](int32_t it) {
                     __syncwarp();
                     const unsigned long long s = item[warp][lane];
-                    if (s) { atomicAdd(a.yacc + bu + it + lane, s); item[warp][lane] = 0; }
+                    if (s) { ycredit(a, bu + it + lane, s); item[warp][lane] = 0; }
                     __syncwarp();
                 });
             __syncwarp();
@@ -1099,7 +1106,7 @@ k_cycles_small(CycleArgs a) {
         };
         auto credit = [&](int k, int32_t q, int32_t y, bool ok, bool live) {
             const uint32_t c = ok ? sm_find(keys, vals, a.capmask, y) : 0;
-            if (c > 1) atomicAdd(a.yacc + q, (unsigned long long)(c - 1));
+            if (c > 1) ycredit(a, q, (unsigned long long)(c - 1));
             item_add(item[warp], k, c > 1 ? c - 1 : 0, live);
         };
         if (du <= SMALL_PCAP) {
@@ -1112,7 +1119,7 @@ k_cycles_small(CycleArgs a) {
                 walk_range(a, u, bu, du, pre, w_lo, w_hi, credit, [&](int32_t j) {
                     __syncwarp();
                     const unsigned long long sv = item[warp][lane];
-                    if (sv) { atomicAdd(a.yacc + bu + j, sv); item[warp][lane] = 0; }
+                    if (sv) { ycredit(a, bu + j, sv); item[warp][lane] = 0; }
                     __syncwarp();
                 });
                 __syncthreads();
@@ -1125,7 +1132,7 @@ k_cycles_small(CycleArgs a) {
                     [&](int32_t it) {
                         __syncwarp();
                         const unsigned long long sv = item[warp][lane];
-                        if (sv) { atomicAdd(a.yacc + bu + it + lane, sv); item[warp][lane] = 0; }
+                        if (sv) { ycredit(a, bu + it + lane, sv); item[warp][lane] = 0; }
                         __syncwarp();
                     });
                 __syncthreads();
@@ -1268,7 +1275,7 @@ k_cycles_medium(CycleArgs a) {
         };
         auto credit = [&](int k, int32_t q, int32_t y, bool ok, bool live) {
             const uint32_t c = ok ? mh_get(tab, cap, y) : 0;
-            if (c > 1) atomicAdd(a.yacc + q, (unsigned long long)(c - 1));
+            if (c > 1) ycredit(a, q, (unsigned long long)(c - 1));
             item_add(item[warp], k, c > 1 ? c - 1 : 0, live);
         };
         // the same for two wedges per lane, their probes in flight together
@@ -1283,8 +1290,8 @@ k_cycles_medium(CycleArgs a) {
                            int k1, int32_t q1, int32_t y1, bool ok1, bool live1) {
             uint32_t c0, c1;
             mh_get2(tab, cap, y0, ok0, y1, ok1, c0, c1);
-            if (c0 > 1) atomicAdd(a.yacc + q0, (unsigned long long)(c0 - 1));
-            if (c1 > 1) atomicAdd(a.yacc + q1, (unsigned long long)(c1 - 1));
+            if (c0 > 1) ycredit(a, q0, (unsigned long long)(c0 - 1));
+            if (c1 > 1) ycredit(a, q1, (unsigned long long)(c1 - 1));
             item_add(item[warp], k0, c0 > 1 ? c0 - 1 : 0, live0);
             item_add(item[warp], k1, c1 > 1 ? c1 - 1 : 0, live1);
         };
@@ -1299,7 +1306,7 @@ k_cycles_medium(CycleArgs a) {
                     walk_range2(a, u, bu, du, pre, w_lo, w_hi, credit2, [&](int32_t j) {
                         __syncwarp();
                         const unsigned long long sv = item[warp][lane];
-                        if (sv) { atomicAdd(a.yacc + bu + j, sv); item[warp][lane] = 0; }
+                        if (sv) { ycredit(a, bu + j, sv); item[warp][lane] = 0; }
                         __syncwarp();
                     });
                 }
@@ -1313,7 +1320,7 @@ k_cycles_medium(CycleArgs a) {
                     [&](int32_t it) {
                         __syncwarp();
                         const unsigned long long sv = item[warp][lane];
-                        if (sv) { atomicAdd(a.yacc + bu + it + lane, sv); item[warp][lane] = 0; }
+                        if (sv) { ycredit(a, bu + it + lane, sv); item[warp][lane] = 0; }
                         __syncwarp();
                     });
                 __syncthreads();
@@ -1377,7 +1384,7 @@ k_cycles_medium_cl(CycleArgs a, int32_t nv_big) {
         };
         auto credit = [&](int k, int32_t q, int32_t y, bool ok, bool live) {
             const uint32_t c = ok ? mh_get(tab, cap, y) : 0;
-            if (c > 1) atomicAdd(a.yacc + q, (unsigned long long)(c - 1));
+            if (c > 1) ycredit(a, q, (unsigned long long)(c - 1));
             item_add(item[warp], k, c > 1 ? c - 1 : 0, live);
         };
         // the same for two wedges per lane, their probes in flight together
@@ -1392,8 +1399,8 @@ k_cycles_medium_cl(CycleArgs a, int32_t nv_big) {
                            int k1, int32_t q1, int32_t y1, bool ok1, bool live1) {
             uint32_t c0, c1;
             mh_get2(tab, cap, y0, ok0, y1, ok1, c0, c1);
-            if (c0 > 1) atomicAdd(a.yacc + q0, (unsigned long long)(c0 - 1));
-            if (c1 > 1) atomicAdd(a.yacc + q1, (unsigned long long)(c1 - 1));
+            if (c0 > 1) ycredit(a, q0, (unsigned long long)(c0 - 1));
+            if (c1 > 1) ycredit(a, q1, (unsigned long long)(c1 - 1));
             item_add(item[warp], k0, c0 > 1 ? c0 - 1 : 0, live0);
             item_add(item[warp], k1, c1 > 1 ? c1 - 1 : 0, live1);
         };
@@ -1406,7 +1413,7 @@ k_cycles_medium_cl(CycleArgs a, int32_t nv_big) {
                 walk_range2(a, u, bu, du, pre, w_lo, w_hi, credit2, [&](int32_t j) {
                     __syncwarp();
                     const unsigned long long sv = item[warp][lane];
-                    if (sv) { atomicAdd(a.yacc + bu + j, sv); item[warp][lane] = 0; }
+                    if (sv) { ycredit(a, bu + j, sv); item[warp][lane] = 0; }
                     __syncwarp();
                 });
                 cl.sync();
@@ -1419,7 +1426,7 @@ k_cycles_medium_cl(CycleArgs a, int32_t nv_big) {
                     [&](int32_t i0) {
                         __syncwarp();
                         const unsigned long long sv = item[warp][lane];
-                        if (sv) { atomicAdd(a.yacc + bu + i0 + lane, sv); item[warp][lane] = 0; }
+                        if (sv) { ycredit(a, bu + i0 + lane, sv); item[warp][lane] = 0; }
                         __syncwarp();
                     });
                 cl.sync();
@@ -1510,7 +1517,7 @@ __device__ __forceinline__ void hub_groups(const CycleArgs &a, int32_t q0, int32
 #pragma unroll
         for (int i = 0; i < G; i++)
             if (c[i] > 1) {
-                atomicAdd(a.yacc + q0 + i * WARP, (unsigned long long)(c[i] - 1));
+                ycredit(a, q0 + i * WARP, (unsigned long long)(c[i] - 1));
                 acc += c[i] - 1;
             }
     }
@@ -1629,7 +1636,7 @@ k_cycles_hub(CycleArgs a) {
                 if (ok) atomicAdd(tab + y, 1u);      // result unused: a reduction
             } else {
                 const uint32_t c = ok ? __ldcg(tab + y) : 0;
-                if (c > 1) atomicAdd(a.yacc + q, (unsigned long long)(c - 1));
+                if (c > 1) ycredit(a, q, (unsigned long long)(c - 1));
                 item_add(item[warp], k, c > 1 ? c - 1 : 0, live);
             }
             w0 += WARP;
@@ -1641,7 +1648,7 @@ k_cycles_hub(CycleArgs a) {
             }
             __syncwarp();
             const unsigned long long s = item[warp][lane];
-            if (s) { atomicAdd(a.yacc + slot_uv, s); item[warp][lane] = 0; }
+            if (s) { ycredit(a, slot_uv, s); item[warp][lane] = 0; }
             __syncwarp();
         }
     }
@@ -2242,8 +2249,11 @@ cudaError_t run_cycles(gd_graph *g, bool per_edge, const int32_t *cnt) {
     const int sms = sms_of(g);
     if (g->m == 0) return cudaSuccess;
     cudaError_t e;
+    // per-slot credits in 32-bit words when they cannot pass 2^32: a slot's
+    // total is at most the 4-cycles through its edge, <= (d_u - 1)(d_v - 1)
+    w.yacc32 = per_edge && g->max_deg <= 65536;
     if (per_edge) {
-        e = cudaMemsetAsync(w.yacc, 0, sizeof(uint64_t) * g->nnz, g->stream);
+        e = cudaMemsetAsync(w.yacc, 0, (w.yacc32 ? sizeof(uint32_t) : sizeof(uint64_t)) * g->nnz, g->stream);
         if (e) return e;
     }
     CycleArgs a;
@@ -2252,6 +2262,7 @@ cudaError_t run_cycles(gd_graph *g, bool per_edge, const int32_t *cnt) {
     a.capmask = (uint32_t)(g->ctx->opt.smem_table_max - 1);
     a.tables = w.wtab; a.mtab = w.mtab; a.mcap = w.mtab_cap; a.west = w.west; a.status = w.status;
     a.yacc = (unsigned long long *)w.yacc; a.sums = w.sums;
+    a.y32 = w.yacc32 ? reinterpret_cast<uint32_t *>(w.yacc) : nullptr;
     a.hub0 = 0; a.nhub = 0;
     // hubs, in batches, over one flat wedge prefix of all hubs
     const int32_t nh = cnt[C_HUB], B = std::min<int32_t>(hub_batch(g), w.wtab_ctas);   // tables allocated

@@ -126,6 +126,26 @@ def test_bipartite_hubs_closed_form(ctxs, mode):
             assert h.count_global() == closed_bipartite(a, b), (a, b)
 
 
+@pytest.mark.parametrize("mode", ["pull_always", gd.GD_VARIANT_ORIENTED])
+def test_per_edge_above_degree_65536(ctxs, mode):
+    """Per-edge counts with a node of degree > 65536: the library keeps its
+    per-slot 4-cycle credits in 64-bit words then (32-bit ones below, where
+    no slot's total can reach 2^32).  Three hubs joined to 70,000 leaves that
+    also form a random graph of their own, against the O2 oracle per edge."""
+    rng = np.random.default_rng(17)
+    leaves = 70_000
+    edges = [(h, 3 + j) for h in range(3) for j in range(leaves)]
+    a = rng.integers(0, leaves, 140_000)
+    b = rng.integers(0, leaves, 140_000)
+    edges += [(3 + int(x), 3 + int(y)) for x, y in zip(a, b) if x != y]
+    g = inputs.from_edges(3 + leaves, edges)
+    assert int(np.diff(g.row_ptr).max()) > 65536
+    with ctxs[mode].graph(g) as h:
+        pe, glob = h.count_per_edge()
+    assert glob == oracle.o2_global(g)
+    assert np.array_equal(pe, oracle.o2_per_edge(g))
+
+
 def test_repeated_calls_identical(ctxs):
     g = inputs.barabasi_albert(5000, 4, 9)
     with ctxs[gd.GD_VARIANT_ORIENTED].graph(g) as h:
