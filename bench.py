@@ -195,8 +195,9 @@ def algorithmic_bytes(g, triangles: int, per_edge: bool, pull_batches: int = 0, 
       for every lower neighbour v the whole list N(v) scanned (8 B per entry,
       W = sum over edges of the smaller degree); one counter update per live
       wedge (y ranked below u; L wedges, 4 B).  The per-edge credit pass
-      repeats the scan, reads each live counter (4 B), credits (v,y) (8 B)
-      and credits each (u,v) once (8 B).
+      repeats the scan, reads each live counter (4 B), credits (v,y) and
+      credits each (u,v) once (a credit word each: 4 B when the largest
+      degree is at most 65536, as the library keeps them then, else 8 B).
     cycles, pull form (hub batches in decreasing rank: for global counts the
       first pull_batches batches of 64 hubs; for per-edge credits the batches
       of `hub_batch` hubs with at least 2 nnz wedges, whose counts the pull
@@ -245,7 +246,8 @@ def algorithmic_bytes(g, triangles: int, per_edge: bool, pull_batches: int = 0, 
     bitmap = passes * (12 * m + 4 * X) + triangles * (20 + (36 if per_edge else 0))
     cycles = 16 * m + 8 * (W - Wp) + 4 * (L - Lp) + pull_bytes
     if per_edge:
-        cycles += 16 * m + 8 * W + 12 * L + 8 * m
+        cw = 4 if int(d.max(initial=0)) <= 65536 else 8     # credit words (32-bit below degree 2^16)
+        cycles += 16 * m + 8 * W + (4 + cw) * L + cw * m
     return {"bitmap": bitmap, "cycles": cycles, "W": W, "L": L, "X": X, "m": m,
             "pulled_hub_wedges": Wp, "pull_batches": npull if pull_batches else 0}
 
