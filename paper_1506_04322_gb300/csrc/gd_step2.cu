@@ -481,7 +481,7 @@ k_clique_bitmap(CliqueArgs a) {
 
     const int32_t nv = a.counters[C_CL0 + a.bucket];
     const int32_t *list = a.clist + (int64_t)a.bucket * a.n;
-    unsigned long long k4_local = 0;   // 3 x 4-cliques (COUNT)
+    unsigned long long k4_local = 0;   // 4-cliques (COUNT)
 
     // warp teams claim CH consecutive list positions per atomic (one counter
     // for ~a million small nodes would serialise on it); CTA teams one
@@ -650,9 +650,23 @@ k_clique_bitmap(CliqueArgs a) {
                 if (MODE != MODE_COUNT) {
                     for (int32_t w = 0; w < Wd; w++) kq += __popc(S.M[kc * Ws + w] & S.M[kx * Ws + w]);
                 } else {
+                    // global count: each 4-clique {a, c, x, d} once, from its
+                    // triangle whose third inner node d comes after both c and
+                    // x in N+(a) (the bits of positions > max(kc, kx))
                     const uint4 *rc = reinterpret_cast<const uint4 *>(S.M + kc * Ws);
                     const uint4 *rx = reinterpret_cast<const uint4 *>(S.M + kx * Ws);
-                    for (int32_t w = 0; w < (Wd + 3) >> 2; w++) {
+                    const int32_t from = max(kc, kx) + 1, nw4 = (Wd + 3) >> 2;
+                    int32_t w = from >> 7;
+                    if (w < nw4) {
+                        const int32_t b = from & 127, wi = b >> 5;
+                        const uint32_t mb = 0xffffffffu << (b & 31);
+                        const uint4 p = rc[w], q = rx[w];
+                        kq += __popc(p.x & q.x & (wi == 0 ? mb : 0u)) +
+                              __popc(p.y & q.y & (wi == 1 ? mb : wi < 1 ? ~0u : 0u)) +
+                              __popc(p.z & q.z & (wi == 2 ? mb : wi < 2 ? ~0u : 0u)) +
+                              __popc(p.w & q.w & (wi == 3 ? mb : ~0u));
+                    }
+                    for (w++; w < nw4; w++) {
                         const uint4 p = rc[w], q = rx[w];
                         kq += __popc(p.x & q.x) + __popc(p.y & q.y) + __popc(p.z & q.z) + __popc(p.w & q.w);
                     }
@@ -697,8 +711,7 @@ k_clique_bitmap(CliqueArgs a) {
         if (threadIdx.x == 0) {
             unsigned long long s = 0;
             for (int w = 0; w < NW; w++) s += red[w];
-            if (s % 3 != 0) atomicOr(a.status, ERR_REMAINDER);
-            add_u128(a.sums + 2 * S_CLIQ, 2ull * s);   // sum_e cliq_e = 6 K4 = 2 (3 K4)
+            add_u128(a.sums + 2 * S_CLIQ, 6ull * s);   // sum_e cliq_e = 6 K4
         }
     }
 }
